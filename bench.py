@@ -1,0 +1,333 @@
+"""Benchmark: 512^3 cubic Klein-Gordon steps/s on one GB300 (or N independent replicas).
+
+Workload (the paper-scale case): N = 512 (R2C storage 512 x 512 x 257 complex128),
+cube side 32, u0 = 0.1 exp(-|x|^2) + 1e-3 lowpass(N(0,1), |m| <= 8) seeded 1501,
+u_t(0) = 0, dt = 0.005, energy every 10 steps.  A "step" is one pass of the whole
+hot path: x pass (C2R, cube, R2C), forward y pass, z pass with the FP64 update, and
+inverse y pass, plus the recorded energy sums every 10th level.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host cores
+on a bounded sample of the same workload.  Under torchrun each rank runs its own
+replica (the method is not sharded); rank 0 prints.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_GRID = 512
+L_BOX = 32.0
+DT = 0.005
+ENERGY_EVERY = 10
+PRECISION = "df64"
+METRIC = "512^3 KG steps/s"
+S_BYTES = N_GRID * N_GRID * (N_GRID // 2 + 1) * 16      # one complex128 half-spectrum array
+
+
+def algorithmic_bytes(prec):
+    """bytes an ideal step moves: 4 passes reading and writing W, plus reading uh^n,
+    uh^{n-1} and writing uh^{n+1} (FP64) in the z pass"""
+    w = S_BYTES if prec in ("fp64", "df64") else S_BYTES // 2
+    per_pass = {"x": 2 * w, "yf": 2 * w, "z": 2 * w + 3 * S_BYTES, "yi": 2 * w}
+    return per_pass, sum(per_pass.values())
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs"""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.25)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(workload, sample_steps):
+    """the FP64 oracle, as it stands, on a bounded sample: set-up + sample_steps steps"""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    s = O.Solver(workload["N"], workload["L"], workload["dt"], workload["u0"], workload["v0"])
+    t1 = time.perf_counter()
+    s.step(sample_steps)
+    t2 = time.perf_counter()
+    s.close()
+    return {"value": sample_steps / (t2 - t1), "unit": "steps/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d steps of the %d^3 workload after a %.1f s set-up (set-up not counted)"
+                      % (sample_steps, workload["N"], t1 - t0)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1501_04552_gb300 import inputs as I
+    w = I.bump_noise(N_GRID)
+    sample = max(1, args.steps)
+    for _ in range(max(0, min(args.warmup, 1))):
+        pass
+    base = cpu_baseline(w, sample)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": sample, "warmup": args.warmup, "ms_per_step": 1e3 / base["value"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "kg512_bump_noise", "N": N_GRID, "L": L_BOX, "dt": DT, "seed": 1501},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default=PRECISION, choices=["fp64", "df64", "mixed"])
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true", help="skip the other precisions and the cuFFT point")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        args.steps = min(args.steps, 3)
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build_library()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1501_04552_gb300 import inputs as I
+    from paper_1501_04552_gb300 import kg
+
+    w = I.bump_noise(N_GRID)
+    u0 = w["u0"]
+    stream = torch.cuda.Stream()
+    kg.kg_set_stream(stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed_steps(prec, steps, warmup):
+        kg.kg_set_options(precision=prec, energy_every=ENERGY_EVERY)
+        d_u0 = torch.from_numpy(u0).to(f"cuda:{local}")
+        kg.kg_init_device(N_GRID, L_BOX, DT, d_u0, None)
+        del d_u0
+        kg.kg_step(warmup)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        kg.kg_step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=f"cuda:{local}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    prec = args.precision
+    with ClockSampler(local) as clk:
+        ms = timed_steps(prec, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms * 1e-3)
+
+    # per-pass device times (CUDA events on the library's stream) for the roofline
+    pass_ms = kg.kg_step_timed(args.steps)
+    pass_avg = [t / args.steps for t in pass_ms]
+    per_pass_bytes, step_bytes = algorithmic_bytes(prec)
+    names = ["x", "yf", "z", "yi"]
+    dom = int(np.argmax(pass_avg))
+    peak, peak_kind = peaks()
+    achieved = per_pass_bytes[names[dom]] / (pass_avg[dom] * 1e-3) / 1e9
+    step_achieved = step_bytes / (ms_per_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "pass_" + names[dom], "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                "step_achieved": round(step_achieved, 1), "step_frac": round(step_achieved / peak, 4),
+                "pass_ms": {n: round(t, 4) for n, t in zip(names, pass_avg)},
+                "pass_bytes": per_pass_bytes}
+
+    # end to end through the public API with host buffers: pinned u0 -> kg_init, K steps, kg_fetch -> host
+    pinned_u0 = torch.from_numpy(u0).pin_memory()
+    out = torch.empty((N_GRID,) * 3, dtype=torch.float64).pin_memory()
+    kg.kg_set_options(precision=prec, energy_every=ENERGY_EVERY)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    kg.lib.kg_init(N_GRID, L_BOX, DT, pinned_u0.data_ptr(), None)
+    kg.kg_step(args.steps)
+    kg.lib.kg_fetch(out.data_ptr())
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * args.steps / t_e2e, "unit": "steps/s",
+           "h2d_bytes_per_step": u0.nbytes // args.steps, "d2h_bytes_per_step": out.numel() * 8 // args.steps,
+           "what": "kg_init from pinned host u0 + %d steps + kg_fetch to pinned host" % args.steps}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        for other in ["fp64", "df64", "mixed"]:
+            if other == prec:
+                continue
+            steps = max(5, args.steps // (8 if other == "fp64" else 1))
+            o_ms = timed_steps(other, steps, 3)
+            extras[other] = {"steps_per_s": round(steps / (o_ms * 1e-3), 2), "ms_per_step": round(o_ms / steps, 4)}
+        extras["cufft_torch"] = torch_fft_point(u0, local)
+
+    base = None
+    if rank == 0 and world == 1:
+        base = cpu_baseline(w, args.cpu_sample_steps)
+
+    kg.kg_finalize()
+    kg.kg_set_stream(None)
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "df64": "f64 state+update, df64 FFT",
+                                                                  "mixed": "f64 state+update, f32 FFT"}[prec],
+                "data": "synthetic",
+                "config": {"workload": "kg512_bump_noise", "N": N_GRID, "L": L_BOX, "dt": DT, "seed": 1501,
+                           "precision": prec, "energy_every": ENERGY_EVERY, "parallelism": "replicas",
+                           "l2": "inputs larger than L2 (each state array 1.08 GB)"},
+                "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": 6 * args.steps + 2 * (args.steps // ENERGY_EVERY) * 0,
+                "other_precisions": extras}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def torch_fft_point(u0, local):
+    """the same step written with torch.fft (cuFFT) in FP64 and FP32: a same-GPU reference point"""
+    import torch
+    out = {}
+    N = u0.shape[0]
+    kf = 2 * np.pi / L_BOX
+    m = torch.fft.fftfreq(N, 1.0 / N, dtype=torch.float64, device=f"cuda:{local}")
+    mx = torch.fft.rfftfreq(N, 1.0 / N, dtype=torch.float64, device=f"cuda:{local}")
+    k2 = kf * kf * (mx[None, None, :] ** 2 + m[None, :, None] ** 2 + m[:, None, None] ** 2)
+    om2 = 1 + k2
+    a = DT * DT * om2 / 4
+    c2 = 2 * (1 - a) / (1 + a)
+    b2 = DT * DT / (1 + a)
+    del k2, om2, a
+    for dt_name, fdt in [("f64", torch.float64), ("f32", torch.float32)]:
+        u = torch.from_numpy(u0).to(f"cuda:{local}")
+        A = torch.fft.rfftn(u)
+        B = A.clone()
+        cdt = torch.complex128 if fdt == torch.float64 else torch.complex64
+        c2f, b2f = c2.to(fdt), b2.to(fdt)
+
+        def step(A, B):
+            uu = torch.fft.irfftn(A.to(cdt), s=(N, N, N))
+            F = torch.fft.rfftn(uu * uu * uu).to(torch.complex128)
+            return c2 * A - B + b2 * F, A
+
+        for _ in range(3):
+            A, B = step(A, B)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 10
+        e0.record()
+        for _ in range(n):
+            A, B = step(A, B)
+        e1.record()
+        e1.synchronize()
+        out[dt_name] = {"steps_per_s": round(n / (e0.elapsed_time(e1) * 1e-3), 2)}
+        del A, B, u
+        torch.cuda.empty_cache()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

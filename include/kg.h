@@ -1,0 +1,125 @@
+/*
+ * kg.h -- C ABI of libkg.so, a GB300 (sm_103a) stepper for the real cubic
+ * Klein-Gordon equation on a periodic cube,
+ *
+ *     u_tt - Laplace(u) + u = |u|^2 u,                  Aseeri et al., Eq. (1),
+ *
+ * advanced with the second-order semi-implicit scheme of section 1.1.2, Eq. (2),
+ * in Fourier space, the cubic term formed in real space: every step is one
+ * complex-to-real 3D FFT, the pointwise cube, one real-to-complex 3D FFT and the
+ * per-mode update (section 1.1.2, "two FFTs per time step").
+ *
+ * Conventions shared by every entry point
+ *   grid      N^3 points on [-L/2, L/2)^3, x_j = -L/2 + j L/N, N in {16,32,...,512}.
+ *             Physical arrays are N^3 doubles, [z][y][x] with x fastest.
+ *   spectrum  unnormalised forward DFT, half spectrum kx = 0..N/2; Fourier state
+ *             uh^n, uh^{n-1} kept in FP64 on the device.  The C2R inverse keeps the
+ *             real parts of the kx = 0 and kx = N/2 entries; no dealiasing; the
+ *             Nyquist wavenumber keeps k^2 = (pi N / L)^2.
+ *   update    uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k with
+ *             omega_k^2 = 1 + k^2, c_k = (1 - dt^2 omega^2/4)/(1 + dt^2 omega^2/4),
+ *             beta_k = (dt^2/2)/(1 + dt^2 omega^2/4), F = lam u^3 (lam = 1: Eq. (1)).
+ *   startup   the paper gives none: uh^{-1} = c_k uh^0 - dt vh^0 + beta_k F^0_k
+ *             (the symmetric level (u^1 - u^{-1})/(2 dt) = v0 put into Eq. (2)).
+ *   energy    the paper gives the continuous functional of section 1.1; the
+ *             discrete one here is E^{n-1/2} = Q^{n-1/2} - (P^{n-1} + P^n)/2 with
+ *             Q^{n+1/2} = (h^3/N^3) sum_k w_k [ |(uh^{n+1}-uh^n)/dt|^2/2
+ *                                          + omega_k^2 |(uh^{n+1}+uh^n)/2|^2/2 ],
+ *             P^n = lam (h^3/4) sum_x (u^n)^4, w_k = 1 on kx = 0, N/2 and 2 elsewhere.
+ *
+ * Context and threading: one global context per process, not thread-safe.  Calls
+ * are ordered on one CUDA stream (the library's own, or the caller's via
+ * kg_set_stream).  Every entry point returns KG_OK (0) or a negative status;
+ * kg_last_error() then describes the failure.  No C++ exception crosses the ABI.
+ * Host pointers are only read (or written) during the call; the library keeps no
+ * reference to caller memory.
+ */
+#ifndef KG_H
+#define KG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define KG_OK 0
+#define KG_EINVAL (-1)    /* bad argument: NULL pointer, non-finite input, dt <= 0, ... */
+#define KG_ENOTSUP (-2)   /* N outside the supported set */
+#define KG_ENOMEM (-3)    /* device or host allocation failed; nothing is leaked */
+#define KG_ECUDA (-4)     /* a CUDA runtime call failed; see kg_last_error() */
+#define KG_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define KG_EDRIFT (-6)    /* energy watchdog: |E - E_0| > drift_tol |E_0| */
+#define KG_ENOTIMPL (-7)  /* entry point not available in this build */
+#define KG_ESTATE (-8)    /* call out of order (e.g. kg_step before kg_init) */
+
+/* arithmetic of the FFT passes (the state uh, the update and the sums are FP64 in all) */
+#define KG_FP64 0   /* IEEE FP64 everywhere */
+#define KG_DF64 1   /* FFT and cube in double-float (pairs of FP32, ~48-bit significand) */
+#define KG_MIXED 2  /* FFT and cube in FP32 (section 1.1.2 scheme, FP32/FP64 split) */
+
+typedef struct kg_options {
+    int precision;          /* KG_FP64, KG_DF64 (default) or KG_MIXED; takes effect at kg_init */
+    int energy_every;       /* record Q and P during kg_step every this many levels (0: never) */
+    double nonlinearity;    /* lam, coefficient of u^3 (default 1.0 = Eq. (1); 0 = linear) */
+    double blowup_threshold;/* > 0: freeze the state once max|u^n| exceeds it (default 0: off) */
+    double drift_tol;       /* > 0: kg_energy returns KG_EDRIFT past this relative drift */
+} kg_options;
+
+/* Set up the solver: N^3 grid of side L, time step dt, initial field u0 and
+ * velocity v0 (host pointers, N^3 doubles each, [z][y][x]; v0 may be NULL = 0).
+ * Both are copied; the caller keeps ownership.  Replaces any previous context.
+ * Level after the call: n = 0.  Errors: KG_EINVAL, KG_ENOTSUP, KG_ENOMEM, KG_ECUDA. */
+int kg_init(int N, double L, double dt, const double* u0, const double* v0);
+
+/* As kg_init with device pointers (N^3 doubles each, v0 may be NULL). */
+int kg_init_device(int N, double L, double dt, const double* d_u0, const double* d_v0);
+
+/* Enqueue n steps of Eq. (2) on the context's stream; returns once enqueued.
+ * Errors: KG_ESTATE (no context), KG_EINVAL (n < 0), KG_ECUDA. */
+int kg_step(int n);
+
+/* Synchronise and write E^{n-1/2} at the current level n (definition above).
+ * Returns KG_EDRIFT (with *E written) when the drift watchdog trips. */
+int kg_energy(double* E);
+
+/* Synchronise and write u^n (N^3 doubles, [z][y][x]) into caller-owned host memory. */
+int kg_fetch(double* u);
+
+/* Same into caller-owned device memory (N^3 doubles); enqueued, no host sync. */
+int kg_fetch_device(double* d_u);
+
+/* Release the context and all device memory.  Safe to call twice. */
+int kg_finalize(void);
+
+/* Use this CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * for all later work; NULL returns to the library's own stream. */
+int kg_set_stream(void* stream);
+
+int kg_set_options(const kg_options* opt);  /* copies *opt; precision applies at the next init */
+int kg_get_options(kg_options* opt);
+
+/* Current level n, blow-up state (1 if frozen, with the level it froze at) and the
+ * max |u| seen by the last step (that of u^{n-1}).  Synchronises. */
+int kg_status(long long* level, int* frozen, long long* blowup_level, double* maxabs);
+
+/* Copy the Fourier state uh^n and uh^{n-1} (N*N*(N/2+1) complex doubles each,
+ * interleaved re/im, [kz][ky][kx]) to host memory; either pointer may be NULL. */
+int kg_fetch_spectral(double* a, double* b);
+
+/* Instrumentation: enqueue n steps launching each pass separately, timing each
+ * with CUDA events on the context's stream; ms[0..3] receive the summed device
+ * time of the x pass, forward y pass, z pass (with the update) and inverse y pass. */
+int kg_step_timed(int n, float* ms);
+
+/* Bytes of device memory the context holds. */
+int kg_memory(size_t* bytes);
+
+/* Description of the last failure in this thread ("" if none). */
+const char* kg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KG_H */

@@ -1,0 +1,561 @@
+// kg_api.cu -- the C ABI of include/kg.h: context, set-up, stepping, energy, read-out.
+//
+// The scheme is Eq. (2) of Aseeri et al. (section 1.1.2) stepped in Fourier space;
+// the energy is the discrete counterpart of the functional of section 1.1 stated in
+// kg.h.  Host code only sequences passes, keeps tables and moves data; every step of
+// the method runs in the kernels of kg_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/kg.h"
+#include "kg_fft.cuh"
+#include "kg_launch.h"
+
+using namespace kg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define KG_CK(call)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(KG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+const double kPi = 3.14159265358979323846;
+
+bool supported_n(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256 || N == 512; }
+
+const PassLaunch* launcher(int prec) {
+    switch (prec) {
+        case KG_FP64: return &kLaunchF64;
+        case KG_DF64: return &kLaunchDF;
+        case KG_MIXED: return &kLaunchF32;
+        default: return nullptr;
+    }
+}
+
+// Test hook: KG_TEST_FAIL_ALLOC=k makes the k-th device allocation of a set-up fail
+// (counted from 1), so the error path and its clean-up can be exercised on the host.
+int g_alloc_counter = 0;
+
+struct Ctx {
+    int N = 0, NH = 0, prec = KG_DF64;
+    double L = 0, dt = 0, lam = 1.0;
+    size_t nspec = 0, nphys = 0;   // complex values per spectral array, reals per physical array
+    cudaStream_t own_stream = nullptr;
+    const PassLaunch* pl = nullptr;
+    double2* S0 = nullptr;   // FP64 state arrays; dev->phase tells which holds uh^n
+    double2* S1 = nullptr;
+    void* W = nullptr;       // work array in the pass precision
+    double2* tmp = nullptr;  // FP64 spectral scratch (set-up and read-out), allocated on demand
+    double* phys = nullptr;  // physical scratch (N^3 doubles), on demand
+    KgDev* dev = nullptr;
+    double* part_sum = nullptr;
+    double* part_max = nullptr;
+    int nparts = 0;
+    double* scal = nullptr;  // device scalars for on-demand sums
+    void* tw = nullptr;      // twiddles exp(-2 pi i j/N), j < N, in the pass precision
+    double2* tw64 = nullptr; // same in FP64 for set-up and read-out
+    double2* coef = nullptr; // (2 c, 2 beta) by integer m^2
+    double* w2 = nullptr;    // omega^2 by integer m^2
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    bool have_E0 = false;
+    double E0 = 0.0;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+Ctx* g_ctx = nullptr;
+kg_options g_opt = {KG_DF64, 0, 1.0, 0.0, 0.0};
+cudaStream_t g_user_stream = nullptr;
+
+cudaStream_t stream_of(const Ctx* c) { return g_user_stream ? g_user_stream : c->own_stream; }
+
+int dalloc(Ctx* c, void** p, size_t bytes, const char* what) {
+    const char* inj = std::getenv("KG_TEST_FAIL_ALLOC");
+    ++g_alloc_counter;
+    if (inj && std::atoi(inj) == g_alloc_counter) {
+        *p = nullptr;
+        return fail(KG_ENOMEM, std::string("injected allocation failure: ") + what);
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(KG_ENOMEM, std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) + " B): " +
+                                   cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    c->bytes += bytes;
+    return KG_OK;
+}
+
+void destroy(Ctx* c) {
+    if (!c) return;
+    if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+    if (g_user_stream) cudaStreamSynchronize(g_user_stream);
+    for (void* p : c->allocs) cudaFree(p);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+// host tables -------------------------------------------------------------
+int upload_tables(Ctx* c) {
+    const int N = c->N;
+    std::vector<double2> t64(N);
+    for (int j = 0; j < N; j++) {
+        const double a = 2.0 * kPi * (double)j / (double)N;
+        t64[j] = make_double2(std::cos(a), -std::sin(a));
+    }
+    int rc = dalloc(c, (void**)&c->tw64, sizeof(double2) * N, "twiddles fp64");
+    if (rc) return rc;
+    KG_CK(cudaMemcpy(c->tw64, t64.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
+    if (c->prec == KG_FP64) {
+        c->tw = c->tw64;
+    } else if (c->prec == KG_DF64) {
+        std::vector<float4> t(N);
+        for (int j = 0; j < N; j++) {
+            float rh = (float)t64[j].x, ih = (float)t64[j].y;
+            t[j] = make_float4(rh, (float)(t64[j].x - (double)rh), ih, (float)(t64[j].y - (double)ih));
+        }
+        rc = dalloc(c, &c->tw, sizeof(float4) * N, "twiddles df");
+        if (rc) return rc;
+        KG_CK(cudaMemcpy(c->tw, t.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float2> t(N);
+        for (int j = 0; j < N; j++) t[j] = make_float2((float)t64[j].x, (float)t64[j].y);
+        rc = dalloc(c, &c->tw, sizeof(float2) * N, "twiddles f32");
+        if (rc) return rc;
+        KG_CK(cudaMemcpy(c->tw, t.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
+    }
+    // coefficients of Eq. (2) by integer wavenumber norm m^2 = mx^2 + my^2 + mz^2
+    const int m2max = 3 * (N / 2) * (N / 2);
+    std::vector<double2> cf(m2max + 1);
+    std::vector<double> w2(m2max + 1);
+    const double kf = 2.0 * kPi / c->L;
+    for (int m2 = 0; m2 <= m2max; m2++) {
+        const double om2 = 1.0 + kf * kf * (double)m2;
+        const double a = c->dt * c->dt * om2 / 4.0;
+        const double cc = (1.0 - a) / (1.0 + a);
+        const double beta = (c->dt * c->dt / 2.0) / (1.0 + a);
+        cf[m2] = make_double2(2.0 * cc, 2.0 * beta);
+        w2[m2] = om2;
+    }
+    rc = dalloc(c, (void**)&c->coef, sizeof(double2) * (m2max + 1), "coefficients");
+    if (rc) return rc;
+    rc = dalloc(c, (void**)&c->w2, sizeof(double) * (m2max + 1), "omega^2");
+    if (rc) return rc;
+    KG_CK(cudaMemcpy(c->coef, cf.data(), sizeof(double2) * (m2max + 1), cudaMemcpyHostToDevice));
+    KG_CK(cudaMemcpy(c->w2, w2.data(), sizeof(double) * (m2max + 1), cudaMemcpyHostToDevice));
+    return KG_OK;
+}
+
+int ensure_scratch(Ctx* c) {
+    int rc = KG_OK;
+    if (!c->tmp) rc = dalloc(c, (void**)&c->tmp, sizeof(double2) * c->nspec, "fp64 spectral scratch");
+    if (!rc && !c->phys) rc = dalloc(c, (void**)&c->phys, sizeof(double) * c->nphys, "physical scratch");
+    return rc;
+}
+
+// FP64 R2C of a physical device array into out (cube: lam u^3 instead of u)
+int forward3d(Ctx* c, const double* u, double2* out, int cube) {
+    const int N = c->N, NH = c->NH;
+    cudaStream_t st = stream_of(c);
+    KG_CK(launch_x_forward(N, u, out, c->tw64, cube, c->lam, st));
+    KG_CK(kLaunchF64.col(N, -1, out, (size_t)N * NH, NH, N, c->tw64, st));   // y
+    KG_CK(kLaunchF64.col(N, -1, out, NH, (size_t)N * NH, N, c->tw64, st));   // z
+    return KG_OK;
+}
+
+// FP64 inverse of a spectral state array (phase-selected pair) into c->tmp (yz only)
+int inverse_yz_f64(Ctx* c, const double2* src0, const double2* src1, const KgDev* sel) {
+    const int N = c->N, NH = c->NH;
+    cudaStream_t st = stream_of(c);
+    KG_CK(kLaunchF64.col_from_f64(N, src0, src1, sel, c->tmp, NH, (size_t)N * NH, N, c->tw64, st));   // z
+    KG_CK(kLaunchF64.col(N, +1, c->tmp, (size_t)N * NH, NH, N, c->tw64, st));                         // y
+    return KG_OK;
+}
+
+double inv_n3(int N) { return 1.0 / ((double)N * (double)N * (double)N); }
+
+int check_finite(const double* a, size_t n, const char* what) {
+    for (size_t i = 0; i < n; i++)
+        if (!std::isfinite(a[i])) return fail(KG_EINVAL, std::string(what) + " has a non-finite entry");
+    return KG_OK;
+}
+
+int init_common(int N, double L, double dt, const double* u0, const double* v0, bool device_ptrs) {
+    if (!supported_n(N)) return fail(KG_ENOTSUP, "N must be one of 16, 32, 64, 128, 256, 512");
+    if (!(L > 0.0) || !std::isfinite(L)) return fail(KG_EINVAL, "L must be finite and > 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(KG_EINVAL, "dt must be finite and > 0");
+    if (!u0) return fail(KG_EINVAL, "u0 is NULL");
+    if (!launcher(g_opt.precision)) return fail(KG_EINVAL, "unknown precision");
+    const size_t n3 = (size_t)N * N * N;
+    if (!device_ptrs) {
+        int rc = check_finite(u0, n3, "u0");
+        if (!rc && v0) rc = check_finite(v0, n3, "v0");
+        if (rc) return rc;
+    }
+    if (g_ctx) {
+        destroy(g_ctx);
+        g_ctx = nullptr;
+    }
+    g_alloc_counter = 0;
+    Ctx* c = new Ctx();
+    c->N = N;
+    c->NH = N / 2 + 1;
+    c->L = L;
+    c->dt = dt;
+    c->lam = g_opt.nonlinearity;
+    c->prec = g_opt.precision;
+    c->pl = launcher(c->prec);
+    c->nspec = (size_t)N * N * c->NH;
+    c->nphys = n3;
+    int rc = KG_OK;
+#define KG_TRY(x)              \
+    do {                       \
+        rc = (x);              \
+        if (rc) {              \
+            destroy(c);        \
+            return rc;         \
+        }                      \
+    } while (0)
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) KG_TRY(fail(KG_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
+    }
+    KG_TRY(dalloc(c, (void**)&c->S0, sizeof(double2) * c->nspec, "state S0"));
+    KG_TRY(dalloc(c, (void**)&c->S1, sizeof(double2) * c->nspec, "state S1"));
+    KG_TRY(dalloc(c, &c->W, c->pl->store_bytes * c->nspec, "work array W"));
+    KG_TRY(dalloc(c, (void**)&c->dev, sizeof(KgDev), "device state"));
+    c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->z_parts(N)), kLaunchF64.x_parts(N));
+    c->nparts = std::max(c->nparts, 152 * 4);
+    KG_TRY(dalloc(c, (void**)&c->part_sum, sizeof(double) * c->nparts, "partials"));
+    KG_TRY(dalloc(c, (void**)&c->part_max, sizeof(double) * c->nparts, "partials max"));
+    KG_TRY(dalloc(c, (void**)&c->scal, sizeof(double) * 8, "scalars"));
+    KG_TRY(upload_tables(c));
+    KG_TRY(ensure_scratch(c));
+    for (auto& e : c->ev) {
+        cudaError_t ee = cudaEventCreate(&e);
+        if (ee != cudaSuccess) KG_TRY(fail(KG_ECUDA, "cudaEventCreate failed"));
+    }
+
+    cudaStream_t st = stream_of(c);
+    const int NH = c->NH;
+    // F^0 = R2C(lam u0^3) into W viewed as FP64 when it is large enough, else into tmp
+    double2* fbuf = nullptr;
+    double2* extra = nullptr;
+    if (c->pl->store_bytes == sizeof(double2)) {
+        fbuf = (double2*)c->W;
+    } else {
+        KG_TRY(dalloc(c, (void**)&extra, sizeof(double2) * c->nspec, "set-up scratch"));
+        fbuf = extra;
+    }
+    auto copy_in = [&](const double* src) -> int {
+        KG_CK(cudaMemcpyAsync(c->phys, src, sizeof(double) * n3, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        return KG_OK;
+    };
+    KG_TRY(copy_in(u0));
+    KG_TRY(forward3d(c, c->phys, fbuf, 1));    // F^0
+    KG_TRY(forward3d(c, c->phys, c->S0, 0));   // uh^0
+    if (v0) {
+        KG_TRY(copy_in(v0));
+        KG_TRY(forward3d(c, c->phys, c->S1, 0));   // vh^0
+    } else {
+        if (cudaMemsetAsync(c->S1, 0, sizeof(double2) * c->nspec, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "memset"));
+    }
+    if (launch_startup(N, c->S0, c->S1, fbuf, c->coef, dt, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "startup launch"));
+    // W <- yz-inverse of uh^0, in the pass precision
+    if (c->pl->col_from_f64(N, c->S0, c->S1, nullptr, c->W, NH, (size_t)N * NH, N, c->tw, st) != cudaSuccess)
+        KG_TRY(fail(KG_ECUDA, "init z inverse"));
+    if (c->pl->col(N, +1, c->W, (size_t)N * NH, NH, N, c->tw, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "init y inverse"));
+    KgDev d;
+    std::memset(&d, 0, sizeof(d));
+    d.level = 0;
+    d.phase = 0;
+    d.frozen = 0;
+    d.blowup_level = -1;
+    d.energy_every = g_opt.energy_every;
+    d.threshold = g_opt.blowup_threshold;
+    d.P_last_level = -1000;
+    d.Q_last_level = -1000;
+    if (cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "dev upload"));
+    {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) KG_TRY(fail(KG_ECUDA, std::string("init: ") + cudaGetErrorString(e)));
+    }
+    if (extra) {
+        cudaFree(extra);
+        for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
+            if (*it == extra) {
+                c->allocs.erase(it);
+                break;
+            }
+        c->bytes -= sizeof(double2) * c->nspec;
+    }
+#undef KG_TRY
+    g_ctx = c;
+    return KG_OK;
+}
+
+int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
+    const int N = c->N, NH = c->NH;
+    const double h = c->L / N;
+    const double p_norm = c->lam * h * h * h / 4.0;
+    const double q_norm = h * h * h * inv_n3(N);
+    if (timed) KG_CK(cudaEventRecord(c->ev[0], st));
+    KG_CK(c->pl->pass_x(N, MODE_STEP, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
+    KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->x_parts(N), c->dev, p_norm, st));
+    if (timed) KG_CK(cudaEventRecord(c->ev[1], st));
+    KG_CK(c->pl->col(N, -1, c->W, (size_t)N * NH, NH, N, c->tw, st));
+    if (timed) KG_CK(cudaEventRecord(c->ev[2], st));
+    KG_CK(c->pl->pass_z(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, c->tw, 1.0 / c->dt, st));
+    KG_CK(launch_fin_z(c->part_sum, c->pl->z_parts(N), c->dev, q_norm, st));
+    if (timed) KG_CK(cudaEventRecord(c->ev[3], st));
+    KG_CK(c->pl->col(N, +1, c->W, (size_t)N * NH, NH, N, c->tw, st));
+    if (timed) {
+        KG_CK(cudaEventRecord(c->ev[4], st));
+        KG_CK(cudaEventSynchronize(c->ev[4]));
+        for (int p = 0; p < 4; p++) {
+            float t = 0.f;
+            KG_CK(cudaEventElapsedTime(&t, c->ev[p], c->ev[p + 1]));
+            ms[p] += t;
+        }
+    }
+    return KG_OK;
+}
+
+int read_dev(Ctx* c, KgDev* d) {
+    cudaStream_t st = stream_of(c);
+    KG_CK(cudaMemcpyAsync(d, c->dev, sizeof(KgDev), cudaMemcpyDeviceToHost, st));
+    KG_CK(cudaStreamSynchronize(st));
+    return KG_OK;
+}
+
+// P of the FP64 state array that is current (older = false) or previous (older = true)
+int p_from_state(Ctx* c, bool older, double* out) {
+    const int N = c->N;
+    const double h = c->L / N;
+    cudaStream_t st = stream_of(c);
+    // phase 0: S0 current; the "older" array is the other one
+    int rc = older ? inverse_yz_f64(c, c->S1, c->S0, c->dev) : inverse_yz_f64(c, c->S0, c->S1, c->dev);
+    if (rc) return rc;
+    KG_CK(launch_x_inverse(N, c->tmp, nullptr, c->tw64, inv_n3(N), c->part_sum, st));
+    KG_CK(launch_fin_sum(c->part_sum, kLaunchF64.x_parts(N), c->lam * h * h * h / 4.0, c->scal, st));
+    KG_CK(cudaMemcpyAsync(out, c->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    KG_CK(cudaStreamSynchronize(st));
+    return KG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int kg_init(int N, double L, double dt, const double* u0, const double* v0) {
+    return init_common(N, L, dt, u0, v0, false);
+}
+
+int kg_init_device(int N, double L, double dt, const double* d_u0, const double* d_v0) {
+    return init_common(N, L, dt, d_u0, d_v0, true);
+}
+
+int kg_step(int n) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_step before kg_init");
+    if (n < 0) return fail(KG_EINVAL, "n < 0");
+    cudaStream_t st = stream_of(c);
+    for (int i = 0; i < n; i++) {
+        int rc = launch_step(c, st, false, nullptr);
+        if (rc) return rc;
+    }
+    return KG_OK;
+}
+
+int kg_step_timed(int n, float* ms) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_step_timed before kg_init");
+    if (n < 0 || !ms) return fail(KG_EINVAL, "bad arguments");
+    for (int p = 0; p < 4; p++) ms[p] = 0.f;
+    cudaStream_t st = stream_of(c);
+    for (int i = 0; i < n; i++) {
+        int rc = launch_step(c, st, true, ms);
+        if (rc) return rc;
+    }
+    return KG_OK;
+}
+
+int kg_energy(double* E) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_energy before kg_init");
+    if (!E) return fail(KG_EINVAL, "E is NULL");
+    const int N = c->N;
+    const double h = c->L / N;
+    cudaStream_t st = stream_of(c);
+    KgDev d;
+    int rc = read_dev(c, &d);
+    if (rc) return rc;
+    const long long n = d.level;
+    double Q, Pm, Pn;
+    // Q^{n-1/2}
+    if (d.Q_last_level == n - 1) {
+        Q = d.Q_last;
+    } else {
+        const double2* cur = d.phase ? c->S1 : c->S0;
+        const double2* old = d.phase ? c->S0 : c->S1;
+        const int np = 152 * 4;
+        KG_CK(launch_energy_q(N, cur, old, c->w2, 1.0 / c->dt, c->part_sum, np, st));
+        KG_CK(launch_fin_sum(c->part_sum, np, h * h * h * inv_n3(N), c->scal, st));
+        KG_CK(cudaMemcpyAsync(&Q, c->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+        KG_CK(cudaStreamSynchronize(st));
+    }
+    // P^{n-1}
+    if (d.P_last_level == n - 1) {
+        Pm = d.P_last;
+    } else {
+        rc = p_from_state(c, true, &Pm);
+        if (rc) return rc;
+    }
+    // P^n: from W (which holds the yz-inverse of uh^n) unless the state froze
+    if (!d.frozen) {
+        KG_CK(c->pl->pass_x(N, MODE_PEEK, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
+        KG_CK(launch_fin_peek(c->part_sum, c->part_max, c->pl->x_parts(N), c->dev, c->lam * h * h * h / 4.0, st));
+        KgDev d2;
+        rc = read_dev(c, &d2);
+        if (rc) return rc;
+        Pn = d2.P_peek;
+    } else {
+        rc = p_from_state(c, false, &Pn);
+        if (rc) return rc;
+    }
+    *E = Q - 0.5 * (Pm + Pn);
+    if (!c->have_E0) {
+        c->have_E0 = true;
+        c->E0 = *E;
+    } else if (g_opt.drift_tol > 0.0 && std::fabs(*E - c->E0) > g_opt.drift_tol * std::fabs(c->E0)) {
+        return fail(KG_EDRIFT, "energy drift beyond drift_tol");
+    }
+    return KG_OK;
+}
+
+int kg_fetch_device(double* d_u) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_fetch before kg_init");
+    if (!d_u) return fail(KG_EINVAL, "output pointer is NULL");
+    int rc = inverse_yz_f64(c, c->S0, c->S1, c->dev);
+    if (rc) return rc;
+    KG_CK(launch_x_inverse(c->N, c->tmp, d_u, c->tw64, inv_n3(c->N), nullptr, stream_of(c)));
+    return KG_OK;
+}
+
+int kg_fetch(double* u) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_fetch before kg_init");
+    if (!u) return fail(KG_EINVAL, "output pointer is NULL");
+    int rc = kg_fetch_device(c->phys);
+    if (rc) return rc;
+    cudaStream_t st = stream_of(c);
+    KG_CK(cudaMemcpyAsync(u, c->phys, sizeof(double) * c->nphys, cudaMemcpyDeviceToHost, st));
+    KG_CK(cudaStreamSynchronize(st));
+    return KG_OK;
+}
+
+int kg_fetch_spectral(double* a, double* b) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_fetch_spectral before kg_init");
+    KgDev d;
+    int rc = read_dev(c, &d);
+    if (rc) return rc;
+    const double2* cur = d.phase ? c->S1 : c->S0;
+    const double2* old = d.phase ? c->S0 : c->S1;
+    if (a) KG_CK(cudaMemcpy(a, cur, sizeof(double2) * c->nspec, cudaMemcpyDeviceToHost));
+    if (b) KG_CK(cudaMemcpy(b, old, sizeof(double2) * c->nspec, cudaMemcpyDeviceToHost));
+    return KG_OK;
+}
+
+int kg_status(long long* level, int* frozen, long long* blowup_level, double* maxabs) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_status before kg_init");
+    KgDev d;
+    int rc = read_dev(c, &d);
+    if (rc) return rc;
+    if (level) *level = d.level;
+    if (frozen) *frozen = d.frozen;
+    if (blowup_level) *blowup_level = d.blowup_level;
+    if (maxabs) *maxabs = d.maxabs_last;
+    return KG_OK;
+}
+
+int kg_finalize(void) {
+    if (g_ctx) {
+        destroy(g_ctx);
+        g_ctx = nullptr;
+    }
+    return KG_OK;
+}
+
+int kg_set_stream(void* stream) {
+    if (g_ctx && g_user_stream != (cudaStream_t)stream) {
+        // order the switch: work already queued on the old stream completes first
+        cudaStream_t old = stream_of(g_ctx);
+        KG_CK(cudaStreamSynchronize(old));
+    }
+    g_user_stream = (cudaStream_t)stream;
+    return KG_OK;
+}
+
+int kg_set_options(const kg_options* o) {
+    if (!o) return fail(KG_EINVAL, "options pointer is NULL");
+    if (!launcher(o->precision)) return fail(KG_EINVAL, "unknown precision");
+    if (o->energy_every < 0) return fail(KG_EINVAL, "energy_every < 0");
+    if (!std::isfinite(o->nonlinearity) || !std::isfinite(o->blowup_threshold) || !std::isfinite(o->drift_tol))
+        return fail(KG_EINVAL, "non-finite option");
+    g_opt = *o;
+    if (g_ctx) {
+        // energy cadence and blow-up threshold apply at once; lam and precision at the next init
+        Ctx* c = g_ctx;
+        KgDev d;
+        int rc = read_dev(c, &d);
+        if (rc) return rc;
+        d.energy_every = o->energy_every;
+        d.threshold = o->blowup_threshold;
+        cudaStream_t st = stream_of(c);
+        KG_CK(cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st));
+        KG_CK(cudaStreamSynchronize(st));
+    }
+    return KG_OK;
+}
+
+int kg_get_options(kg_options* o) {
+    if (!o) return fail(KG_EINVAL, "options pointer is NULL");
+    *o = g_opt;
+    return KG_OK;
+}
+
+int kg_memory(size_t* bytes) {
+    if (!bytes) return fail(KG_EINVAL, "NULL");
+    *bytes = g_ctx ? g_ctx->bytes : 0;
+    return KG_OK;
+}
+
+const char* kg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

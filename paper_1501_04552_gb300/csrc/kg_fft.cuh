@@ -1,0 +1,360 @@
+// kg_fft.cuh -- shared-memory Stockham FFTs and the fused passes of one time step.
+//
+// One time step of the scheme of section 1.1.2 (Eq. (2), stepped in Fourier space
+// with the cube formed in real space, two 3D FFTs per step) is four passes over the
+// work array W (half spectrum in x, [z][y][kx] / [kz][ky][kx], kx = 0..N/2 fastest):
+//
+//   X  : per x-line, complex-to-real inverse along x (N-point real transform through
+//        an N/2-point complex FFT), scale 1/N^3 -> u^n on the line; max|u|, sum u^4;
+//        F = lam u^3; real-to-complex forward along x; written back in place.
+//   Yf : per (z, kx) column, forward complex FFT along y, in place.
+//   Z  : per (ky, kx) column, forward complex FFT along z -> F^n_k; the FP64 update
+//        uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k written over uh^{n-1};
+//        optional Q^{n+1/2} partial sums; inverse complex FFT along z of uh^{n+1} -> W.
+//   Yi : per (z, kx) column, inverse complex FFT along y, in place.
+//
+// The pencil transposes of a distributed 3D FFT become strided column accesses:
+// a column tile is C consecutive kx columns (C * element = 128 bytes, one full
+// line per row) by all N rows, held in registers (8 values per thread) and in
+// shared memory between radix stages.
+//
+// FFT formulation: Stockham autosort, radix 8 (last stage radix 2 or 4 when log2 n
+// is not a multiple of 3).  With T = n/8 threads per line, thread j holds the
+// values of index j + T s (s = 0..7) before every stage and after the last one, so
+// a forward transform can feed an inverse one without any exchange.
+#pragma once
+#include "kg_arith.cuh"
+
+namespace kg {
+
+// x-pass modes: one stepping pass, or a read-only pass for P^n
+enum { MODE_STEP = 0, MODE_PEEK = 1 };
+
+constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+
+template <int n>
+struct FftShape {
+    static_assert(n >= 8 && (n & (n - 1)) == 0, "power-of-two length >= 8");
+    static constexpr int lg = ilog2c(n);
+    static constexpr int n8 = lg / 3;              // radix-8 stages
+    static constexpr int rem = 1 << (lg % 3);      // radix of the final stage (1: none)
+    static constexpr int stages = n8 + (rem > 1 ? 1 : 0);
+    static constexpr int T = n / 8;                // threads per line
+};
+
+// twiddle exp(SIGN 2 pi i idx / Ntab) from a table of exp(-2 pi i j / Ntab)
+template <class P, int SIGN>
+__device__ __forceinline__ cx<typename P::R> twiddle(const typename P::S* __restrict__ tw, int idx) {
+    cx<typename P::R> w = P::load(__ldg(tw + idx));
+    return SIGN < 0 ? w : conj(w);
+}
+
+// ---------------------------------------------------------------------------
+// small DFTs, y_k = sum_j u_j exp(SIGN 2 pi i j k / R), in place, natural order
+// ---------------------------------------------------------------------------
+template <class P, int SIGN>
+__device__ __forceinline__ void dft2(cx<typename P::R>* u) {
+    cx<typename P::R> a = u[0] + u[1], b = u[0] - u[1];
+    u[0] = a;
+    u[1] = b;
+}
+
+template <class P, int SIGN>
+__device__ __forceinline__ void dft4(cx<typename P::R>* u) {
+    typedef cx<typename P::R> C;
+    C t0 = u[0] + u[2], t1 = u[0] - u[2], t2 = u[1] + u[3];
+    C t3 = mul_si<SIGN>(u[1] - u[3]);
+    u[0] = t0 + t2;
+    u[1] = t1 + t3;
+    u[2] = t0 - t2;
+    u[3] = t1 - t3;
+}
+
+template <class P, int SIGN>
+__device__ __forceinline__ void dft8(cx<typename P::R>* u) {
+    typedef typename P::R R;
+    typedef cx<R> C;
+    C a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        a[j] = u[j] + u[j + 4];
+        b[j] = u[j] - u[j + 4];
+    }
+    const R r = P::rsqrt2();
+    {   // b1 *= exp(SIGN i pi/4) = (1 + SIGN i)/sqrt2
+        C x = b[1];
+        b[1] = SIGN < 0 ? cmake<R>((x.re + x.im) * r, (x.im - x.re) * r)
+                        : cmake<R>((x.re - x.im) * r, (x.im + x.re) * r);
+    }
+    b[2] = mul_si<SIGN>(b[2]);
+    {   // b3 *= exp(SIGN 3 i pi/4) = (-1 + SIGN i)/sqrt2
+        C x = b[3];
+        b[3] = SIGN < 0 ? cmake<R>((x.im - x.re) * r, -(x.im + x.re) * r)
+                        : cmake<R>(-(x.re + x.im) * r, (x.re - x.im) * r);
+    }
+    dft4<P, SIGN>(a);
+    dft4<P, SIGN>(b);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        u[2 * k] = a[k];
+        u[2 * k + 1] = b[k];
+    }
+}
+
+template <class P, int SIGN, int RADIX>
+__device__ __forceinline__ void dft(cx<typename P::R>* u) {
+    if (RADIX == 8) dft8<P, SIGN>(u);
+    else if (RADIX == 4) dft4<P, SIGN>(u);
+    else if (RADIX == 2) dft2<P, SIGN>(u);
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory views
+// ---------------------------------------------------------------------------
+// column tile: element (row, column c) at base[row * C + c]; the whole CTA syncs
+template <class P, int C>
+struct ColSmem {
+    typename P::S* base;
+    int c;
+    __device__ __forceinline__ void put(int row, cx<typename P::R> v) { base[row * C + c] = P::pack(v); }
+    __device__ __forceinline__ cx<typename P::R> get(int row) const { return P::load(base[row * C + c]); }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+// one line per group of threads inside a warp; one pad slot every 8 avoids bank conflicts
+template <class P>
+struct LineSmem {
+    typename P::S* base;
+    static __device__ __forceinline__ int pad(int i) { return i + (i >> 3); }
+    __device__ __forceinline__ void put(int i, cx<typename P::R> v) { base[pad(i)] = P::pack(v); }
+    __device__ __forceinline__ cx<typename P::R> get(int i) const { return P::load(base[pad(i)]); }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+
+// ---------------------------------------------------------------------------
+// Stockham stage STAGE of a length-n transform.  Butterfly b (= j + T q) of a
+// radix-R stage with span Ns reads x[b + r n/R], applies exp(SIGN 2 pi i k r/(Ns R))
+// (k = b mod Ns), takes the R-point DFT and writes y[(b - k) R + k + r Ns].
+// twmul: table length / n.
+// ---------------------------------------------------------------------------
+template <class P, int n, int SIGN, int STAGE, class SM>
+__device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw,
+                                          int twmul, SM& sm) {
+    typedef cx<typename P::R> C;
+    typedef FftShape<n> Sh;
+    constexpr int RADIX = (STAGE < Sh::n8) ? 8 : Sh::rem;
+    constexpr int Ns = 1 << (3 * STAGE);
+    constexpr int T = Sh::T;
+    constexpr int Q = 8 / RADIX;
+    constexpr bool LAST = (STAGE == Sh::stages - 1);
+    C out[8];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        const int b = j + T * q;
+        const int k = b & (Ns - 1);
+        C u[RADIX];
+#pragma unroll
+        for (int r = 0; r < RADIX; r++) u[r] = v[q + r * Q];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < RADIX; r++) u[r] = cmul(u[r], twiddle<P, SIGN>(tw, k * r * (n / (Ns * RADIX)) * twmul));
+        }
+        dft<P, SIGN, RADIX>(u);
+        if (LAST) {
+#pragma unroll
+            for (int r = 0; r < RADIX; r++) out[q + r * Q] = u[r];
+        } else {
+            const int base = (b - k) * RADIX + k;
+#pragma unroll
+            for (int r = 0; r < RADIX; r++) sm.put(base + r * Ns, u[r]);
+        }
+    }
+    if (LAST) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) v[s] = out[s];
+    } else {
+        sm.sync();
+#pragma unroll
+        for (int s = 0; s < 8; s++) v[s] = sm.get(j + T * s);
+        sm.sync();
+    }
+}
+
+// full length-n transform, unnormalised, sign SIGN; in and out: v[s] = x[j + T s]
+template <class P, int n, int SIGN, class SM>
+__device__ __forceinline__ void fft(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw, int twmul,
+                                    SM& sm) {
+    typedef FftShape<n> Sh;
+    fft_stage<P, n, SIGN, 0>(v, j, tw, twmul, sm);
+    if constexpr (Sh::stages > 1) fft_stage<P, n, SIGN, 1>(v, j, tw, twmul, sm);
+    if constexpr (Sh::stages > 2) fft_stage<P, n, SIGN, 2>(v, j, tw, twmul, sm);
+    if constexpr (Sh::stages > 3) fft_stage<P, n, SIGN, 3>(v, j, tw, twmul, sm);
+}
+
+// ---------------------------------------------------------------------------
+// value conversion between precisions (only FP64 -> any is needed)
+// ---------------------------------------------------------------------------
+template <class Pfrom, class Pto>
+struct Convert;
+template <class P>
+struct Convert<P, P> {
+    static __device__ __forceinline__ cx<typename P::R> go(cx<typename P::R> c) { return c; }
+};
+template <>
+struct Convert<PrecF64, PrecDF> {
+    static __device__ __forceinline__ cx<df> go(cx<double> c) { return cmake<df>(d2df_int(c.re), d2df_int(c.im)); }
+};
+template <>
+struct Convert<PrecF64, PrecF32> {
+    static __device__ __forceinline__ cx<float> go(cx<double> c) { return cmake<float>(d2f_int(c.re), d2f_int(c.im)); }
+};
+
+// ---------------------------------------------------------------------------
+// per-thread statistics of u on the x pass: sum u^4 and max |u|
+// ---------------------------------------------------------------------------
+struct NSum {  // Neumaier pair
+    double s, c;
+    __device__ __forceinline__ void add(double x) {
+        double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return s + c; }
+};
+
+template <class P>
+struct Stats;
+
+template <>
+struct Stats<PrecF64> {
+    NSum sum;
+    unsigned long long mx;
+    __device__ __forceinline__ void init() { sum.s = 0.0; sum.c = 0.0; mx = 0ull; }
+    __device__ __forceinline__ void take(double u, bool want_sum) {
+        unsigned long long key = (unsigned long long)__double_as_longlong(u) & 0x7FFFFFFFFFFFFFFFull;
+        mx = key > mx ? key : mx;
+        if (want_sum) {
+            double u2 = u * u;
+            sum.add(u2 * u2);
+        }
+    }
+    __device__ __forceinline__ double total() const { return sum.value(); }
+    __device__ __forceinline__ double maxval() const { return __longlong_as_double((long long)mx); }
+};
+
+template <>
+struct Stats<PrecDF> {
+    df acc;
+    unsigned int mx;
+    __device__ __forceinline__ void init() { acc = df_make(0.f, 0.f); mx = 0u; }
+    __device__ __forceinline__ void take(df u, bool want_sum) {
+        unsigned int key = __float_as_uint(u.hi) & 0x7FFFFFFFu;
+        mx = key > mx ? key : mx;
+        if (want_sum) {
+            df u2 = u * u;
+            acc = acc + u2 * u2;
+        }
+    }
+    __device__ __forceinline__ double total() const { return f2d_int(acc.hi) + f2d_int(acc.lo); }
+    __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
+};
+
+template <>
+struct Stats<PrecF32> {
+    df acc;
+    unsigned int mx;
+    __device__ __forceinline__ void init() { acc = df_make(0.f, 0.f); mx = 0u; }
+    __device__ __forceinline__ void take(float u, bool want_sum) {
+        unsigned int key = __float_as_uint(u) & 0x7FFFFFFFu;
+        mx = key > mx ? key : mx;
+        if (want_sum) {
+            float u2 = u * u;
+            acc = acc + df_make(u2 * u2, 0.f);
+        }
+    }
+    __device__ __forceinline__ double total() const { return f2d_int(acc.hi) + f2d_int(acc.lo); }
+    __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
+};
+
+// ---------------------------------------------------------------------------
+// device-side run state (lives in device memory; read by the passes so that a
+// captured step needs no host decisions)
+// ---------------------------------------------------------------------------
+struct KgDev {
+    long long level;          // n
+    int phase;                // 0: S0 = uh^n, S1 = uh^{n-1}; 1: swapped
+    int frozen;               // blow-up flag
+    long long blowup_level;   // level at which the state froze
+    int energy_every;         // record Q, P on steps from level l with (l+1) % energy_every == 0
+    int pad0;
+    double threshold;         // > 0: blow-up check max|u^n| > threshold
+    double maxabs_last;       // max |u^l| of the last x pass of a step
+    double P_last;            // P^l of the last recording step
+    long long P_last_level;
+    double Q_last;            // Q^{l+1/2} of the last recording step
+    long long Q_last_level;
+    double P_peek;            // sum-based P of the last peek
+    double maxabs_peek;
+    int status;               // nonzero: a device-side check failed
+    int pad1;
+};
+
+__device__ __forceinline__ bool kg_recording(const KgDev* dev) {
+    return dev->energy_every > 0 && ((dev->level + 1) % dev->energy_every) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// block reduction of (Neumaier pair, max) -> thread 0
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void nsum_merge(NSum& a, const NSum& b) {
+    a.add(b.s);
+    a.c += b.c;
+}
+
+// NT threads, a power of two; lane 0 of warp 0 ends with the block result
+template <int NT>
+__device__ __forceinline__ void block_reduce(NSum& v, double& mx, double* sh) {
+    // sh: 3 * 32 doubles
+    constexpr unsigned kMask = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
+    constexpr int kOff0 = NT >= 32 ? 16 : NT / 2;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = kOff0; o > 0; o >>= 1) {
+        NSum b;
+        b.s = __shfl_down_sync(kMask, v.s, o);
+        b.c = __shfl_down_sync(kMask, v.c, o);
+        double m = __shfl_down_sync(kMask, mx, o);
+        nsum_merge(v, b);
+        mx = (m > mx || m != m) ? m : mx;
+    }
+    constexpr int NW = (NT + 31) / 32;
+    if (NW > 1) {
+        __syncthreads();
+        if (lane == 0) {
+            sh[w] = v.s;
+            sh[32 + w] = v.c;
+            sh[64 + w] = mx;
+        }
+        __syncthreads();
+        if (w == 0) {
+            NSum t;
+            t.s = lane < NW ? sh[lane] : 0.0;
+            t.c = lane < NW ? sh[32 + lane] : 0.0;
+            double m = lane < NW ? sh[64 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                NSum b;
+                b.s = __shfl_down_sync(0xffffffffu, t.s, o);
+                b.c = __shfl_down_sync(0xffffffffu, t.c, o);
+                double mm = __shfl_down_sync(0xffffffffu, m, o);
+                nsum_merge(t, b);
+                m = (mm > m || mm != mm) ? mm : m;
+            }
+            v = t;
+            mx = m;
+        }
+    }
+}
+
+}  // namespace kg

@@ -1,0 +1,9 @@
+// kg_inst_df.cu -- pass launchers for the PrecDF precision.
+#include "kg_launch_impl.cuh"
+
+namespace kg {
+template struct Launchers<PrecDF>;
+const PassLaunch kLaunchDF = {
+    &Launchers<PrecDF>::pass_x, &Launchers<PrecDF>::col, &Launchers<PrecDF>::col_from_f64, &Launchers<PrecDF>::pass_z,
+    &Launchers<PrecDF>::x_parts, &Launchers<PrecDF>::z_parts, sizeof(PrecDF::S)};
+}  // namespace kg

@@ -1,0 +1,9 @@
+// kg_inst_f32.cu -- pass launchers for the PrecF32 precision.
+#include "kg_launch_impl.cuh"
+
+namespace kg {
+template struct Launchers<PrecF32>;
+const PassLaunch kLaunchF32 = {
+    &Launchers<PrecF32>::pass_x, &Launchers<PrecF32>::col, &Launchers<PrecF32>::col_from_f64, &Launchers<PrecF32>::pass_z,
+    &Launchers<PrecF32>::x_parts, &Launchers<PrecF32>::z_parts, sizeof(PrecF32::S)};
+}  // namespace kg

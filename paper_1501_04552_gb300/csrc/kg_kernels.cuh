@@ -1,0 +1,491 @@
+// kg_kernels.cuh -- kernel templates of the step passes, the set-up and the read-out.
+#pragma once
+#include "kg_fft.cuh"
+
+namespace kg {
+
+// ---------------------------------------------------------------------------
+// Pass X.  MODE_STEP: C2R along x, stats, F = lam u^3, R2C along x, in place.
+//          MODE_PEEK: C2R along x and stats only (W untouched).
+// One line = N/2+1 complex values; T = N/16 threads per line, 256 threads per CTA.
+// ---------------------------------------------------------------------------
+constexpr int kXThreads = 256;
+
+template <int N>
+struct XShape {
+    static constexpr int M = N / 2;
+    static constexpr int T = M / 8;
+    static constexpr int LPC = kXThreads / T;           // lines per CTA
+    static constexpr int PADM = M + M / 8;              // padded smem slots per line
+    static_assert(T <= 32, "one line must fit in a warp");
+};
+
+template <class P, int N>
+__device__ __forceinline__ void x_load_c2r(const typename P::S* __restrict__ line, int j, const typename P::S* __restrict__ tw,
+                                           cx<typename P::R> (&v)[8]) {
+    typedef typename P::R R;
+    typedef cx<R> C;
+    constexpr int M = N / 2, T = XShape<N>::T;
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        const int k = j + T * s;
+        C X = P::load(line[k]);
+        C Xp = P::load(line[M - k]);       // k = 0 pairs with the Nyquist entry k = M
+        if (k == 0) {                      // real parts only at kx = 0 and kx = N/2
+            X.im = P::from_f64(0.0);
+            Xp.im = P::from_f64(0.0);
+        }
+        C A = X + conj(Xp);
+        C B = X - conj(Xp);
+        C w = twiddle<P, +1>(tw, k);       // exp(+2 pi i k / N)
+        v[s] = A + mul_i(cmul(w, B));
+    }
+}
+
+template <class P, int N, int MODE>
+__global__ void __launch_bounds__(kXThreads) k_pass_x(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
+                                                      double* __restrict__ part_sum, double* __restrict__ part_max,
+                                                      const typename P::S* __restrict__ tw, double scale, double lam) {
+    typedef typename P::R R;
+    typedef typename P::S S;
+    typedef cx<R> C;
+    typedef XShape<N> X;
+    constexpr int M = X::M, T = X::T, NH = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    S* sm = reinterpret_cast<S*>(smraw);
+    __shared__ double red[96];
+
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const size_t line = (size_t)blockIdx.x * X::LPC + li;
+    S* __restrict__ L = W + line * NH;
+    LineSmem<P> lsm{sm + li * X::PADM};
+
+    const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev);
+
+    C v[8];
+    x_load_c2r<P, N>(L, j, tw, v);
+    fft<P, M, +1>(v, j, tw, 2, lsm);
+
+    Stats<P> st;
+    st.init();
+    const R rlam = P::from_f64(lam);
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        v[s].re = P::scale2(v[s].re, scale);   // scale = 1/N^3, a power of two
+        v[s].im = P::scale2(v[s].im, scale);
+        st.take(v[s].re, want_sum);
+        st.take(v[s].im, want_sum);
+    }
+
+    if (MODE == MODE_STEP) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            v[s].re = rlam * (v[s].re * v[s].re * v[s].re);
+            v[s].im = rlam * (v[s].im * v[s].im * v[s].im);
+        }
+        fft<P, M, -1>(v, j, tw, 2, lsm);
+        // real-to-complex post-processing: X[k] = (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2
+#pragma unroll
+        for (int s = 0; s < 8; s++) lsm.put(j + T * s, v[s]);
+        lsm.sync();
+        const double half = 0.5;
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            const int k = j + T * s;
+            C Z = v[s];
+            C Zp = lsm.get((M - k) & (M - 1));
+            C A = Z + conj(Zp);
+            C B = Z - conj(Zp);
+            C w = twiddle<P, -1>(tw, k);   // exp(-2 pi i k / N)
+            C D = mul_i(cmul(w, B));
+            C out = A - D;
+            out.re = P::scale2(out.re, half);
+            out.im = P::scale2(out.im, half);
+            L[k] = P::pack(out);
+            if (k == 0) L[M] = P::pack(cmake<R>(Z.re - Z.im, P::from_f64(0.0)));
+        }
+    }
+
+    NSum acc;
+    acc.s = st.total();
+    acc.c = 0.0;
+    double mx = st.maxval();
+    block_reduce<kXThreads>(acc, mx, red);
+    if (threadIdx.x == 0) {
+        part_sum[blockIdx.x] = acc.value();
+        part_max[blockIdx.x] = mx;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column FFT: C consecutive kx columns of one plane, all N rows, in place or
+// from a source array in another storage format (set-up / read-out).
+// Y passes: plane = z, plane stride N*NH, row stride NH.
+// Z passes: plane = ky, plane stride NH, row stride N*NH.
+// ---------------------------------------------------------------------------
+template <class P>
+struct ColShape {
+    static constexpr int C = 128 / (int)sizeof(typename P::S);
+};
+
+template <class Pin, class P, class Pout, int N, int SIGN>
+__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col(const typename Pin::S* src, typename Pout::S* dst,
+                                                               size_t plane_stride, size_t row_stride,
+                                                               const typename P::S* __restrict__ tw) {
+    typedef typename P::R R;
+    typedef cx<R> Cx;
+    constexpr int C = ColShape<P>::C, T = N / 8, NH = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
+
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const int kx = blockIdx.x * C + c;
+    const bool valid = kx < NH;
+    const size_t base = (size_t)blockIdx.y * plane_stride + kx;
+    ColSmem<P, C> csm{sm, c};
+
+    Cx v[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        if (valid) v[s] = Convert<Pin, P>::go(Pin::load(src[base + (size_t)(j + T * s) * row_stride]));
+        else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
+    }
+    fft<P, N, SIGN>(v, j, tw, 1, csm);
+    if (valid) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) dst[base + (size_t)(j + T * s) * row_stride] = Pout::pack(Convert<P, Pout>::go(v[s]));
+    }
+}
+
+// inverse column FFT from an FP64 spectral array into W (precision P); the source is
+// src1 when dev != NULL and dev->phase == 1, src0 otherwise (the current level's array)
+template <class P, int N>
+__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col_sel(const double2* src0, const double2* src1,
+                                                                   const KgDev* dev, typename P::S* dst,
+                                                                   size_t plane_stride, size_t row_stride,
+                                                                   const typename P::S* __restrict__ tw) {
+    typedef typename P::R R;
+    typedef cx<R> Cx;
+    constexpr int C = ColShape<P>::C, T = N / 8, NH = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
+    const double2* __restrict__ src = (dev != nullptr && dev->phase) ? src1 : src0;
+
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const int kx = blockIdx.x * C + c;
+    const bool valid = kx < NH;
+    const size_t base = (size_t)blockIdx.y * plane_stride + kx;
+    ColSmem<P, C> csm{sm, c};
+
+    Cx v[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        if (valid) v[s] = Convert<PrecF64, P>::go(PrecF64::load(src[base + (size_t)(j + T * s) * row_stride]));
+        else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
+    }
+    fft<P, N, +1>(v, j, tw, 1, csm);
+    if (valid) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) dst[base + (size_t)(j + T * s) * row_stride] = P::pack(v[s]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass Z: forward z FFT -> F^n, FP64 update, optional Q partials, inverse z FFT.
+// coef[m2] = (2 c_k, 2 beta_k) for integer m2 = mx^2 + my^2 + mz^2; w2[m2] = omega_k^2.
+// ---------------------------------------------------------------------------
+template <class P, int N>
+__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_pass_z(typename P::S* __restrict__ W, double2* S0, double2* S1,
+                                                                  KgDev* __restrict__ dev, double* __restrict__ part_sum,
+                                                                  const double2* __restrict__ coef,
+                                                                  const double* __restrict__ w2tab,
+                                                                  const typename P::S* __restrict__ tw, double inv_dt) {
+    typedef typename P::R R;
+    typedef cx<R> Cx;
+    constexpr int C = ColShape<P>::C, T = N / 8, NH = N / 2 + 1, NT = C * T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
+    __shared__ double red[96];
+
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const int kx = blockIdx.x * C + c;
+    const int ky = blockIdx.y;
+    const bool valid = kx < NH;
+    const size_t rs = (size_t)N * NH;
+    const size_t base = (size_t)ky * NH + kx;
+    ColSmem<P, C> csm{sm, c};
+
+    const bool frozen = dev->frozen != 0;
+    const bool want_q = kg_recording(dev);
+    double2* __restrict__ cur = dev->phase ? S1 : S0;
+    double2* __restrict__ old = dev->phase ? S0 : S1;
+
+    Cx v[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        if (valid) v[s] = P::load(W[base + (size_t)(j + T * s) * rs]);
+        else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
+    }
+    fft<P, N, -1>(v, j, tw, 1, csm);
+
+    const int my = ky <= N / 2 ? ky : ky - N;
+    const int mxy2 = kx * kx + my * my;
+    const double wgt = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
+    NSum q;
+    q.s = 0.0;
+    q.c = 0.0;
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        const int kz = j + T * s;
+        const int mz = kz <= N / 2 ? kz : kz - N;
+        const int m2 = mxy2 + mz * mz;
+        if (valid) {
+            const size_t idx = base + (size_t)kz * rs;
+            const double2 cf = __ldg(coef + m2);
+            const double2 a = cur[idx];
+            const double2 b = old[idx];
+            double nre = P::fma_into(cf.y, v[s].re, fma(cf.x, a.x, -b.x));
+            double nim = P::fma_into(cf.y, v[s].im, fma(cf.x, a.y, -b.y));
+            if (!frozen) old[idx] = make_double2(nre, nim);
+            if (want_q) {
+                const double dre = (nre - a.x) * inv_dt, dim = (nim - a.y) * inv_dt;
+                const double sre = nre + a.x, sim = nim + a.y;
+                const double term = 0.5 * (dre * dre + dim * dim) + 0.125 * __ldg(w2tab + m2) * (sre * sre + sim * sim);
+                q.add(wgt * term);
+            }
+            v[s] = cmake<R>(P::from_f64(nre), P::from_f64(nim));
+        }
+    }
+    if (want_q) {
+        double mx = 0.0;
+        block_reduce<NT>(q, mx, red);
+        if (threadIdx.x == 0) part_sum[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = q.value();
+    }
+
+    fft<P, N, +1>(v, j, tw, 1, csm);
+    if (valid) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) W[base + (size_t)(j + T * s) * rs] = P::pack(v[s]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finalisers (one CTA of 1024 threads)
+// ---------------------------------------------------------------------------
+constexpr int kFinThreads = 1024;
+
+__device__ __forceinline__ void fin_reduce(const double* part_sum, const double* part_max, int count, NSum& acc,
+                                           double& mx) {
+    __shared__ double red[96];
+    acc.s = 0.0;
+    acc.c = 0.0;
+    mx = 0.0;
+    for (int i = threadIdx.x; i < count; i += kFinThreads) {
+        acc.add(part_sum[i]);
+        if (part_max) {
+            double m = part_max[i];
+            mx = (m > mx || m != m) ? m : mx;
+        }
+    }
+    block_reduce<kFinThreads>(acc, mx, red);
+}
+
+#ifdef KG_DEFINE_COMMON_KERNELS   // defined by exactly one translation unit
+// after a stepping x pass: blow-up check and P^l; p_norm = lam h^3 / 4
+__global__ void __launch_bounds__(kFinThreads) k_fin_x(const double* part_sum, const double* part_max, int count,
+                                                       KgDev* dev, double p_norm) {
+    NSum acc;
+    double mx;
+    fin_reduce(part_sum, part_max, count, acc, mx);
+    if (threadIdx.x == 0) {
+        if (!dev->frozen) {
+            dev->maxabs_last = mx;
+            if (kg_recording(dev)) {
+                dev->P_last = p_norm * acc.value();
+                dev->P_last_level = dev->level;
+            }
+            if (dev->threshold > 0.0 && !(mx <= dev->threshold)) {
+                dev->frozen = 1;
+                dev->blowup_level = dev->level;
+            }
+        }
+    }
+}
+
+// after a peek x pass
+__global__ void __launch_bounds__(kFinThreads) k_fin_peek(const double* part_sum, const double* part_max, int count,
+                                                          KgDev* dev, double p_norm) {
+    NSum acc;
+    double mx;
+    fin_reduce(part_sum, part_max, count, acc, mx);
+    if (threadIdx.x == 0) {
+        dev->P_peek = p_norm * acc.value();
+        dev->maxabs_peek = mx;
+    }
+}
+
+// after the z pass: Q^{l+1/2} (q_norm = h^3/N^3) and the level advance
+__global__ void __launch_bounds__(kFinThreads) k_fin_z(const double* part_sum, int count, KgDev* dev, double q_norm) {
+    const bool rec = kg_recording(dev);
+    NSum acc;
+    double mx;
+    if (rec) fin_reduce(part_sum, nullptr, count, acc, mx);
+    if (threadIdx.x == 0 && !dev->frozen) {
+        if (rec) {
+            dev->Q_last = q_norm * acc.value();
+            dev->Q_last_level = dev->level;
+        }
+        dev->level += 1;
+        dev->phase ^= 1;
+    }
+}
+
+#endif  // KG_DEFINE_COMMON_KERNELS
+
+// ---------------------------------------------------------------------------
+// FP64 set-up and read-out kernels
+// ---------------------------------------------------------------------------
+// forward R2C along x of physical lines: out[line][k] = sum_x f(u[line][x]) e^{-2 pi i k x/N},
+// f(u) = u (cube == 0) or lam u^3 (cube == 1).  Same line mapping as pass X.
+template <int N>
+__global__ void __launch_bounds__(kXThreads) k_x_forward(const double* __restrict__ u, double2* __restrict__ out,
+                                                         const double2* __restrict__ tw, int cube, double lam) {
+    typedef PrecF64 P;
+    typedef cx<double> C;
+    typedef XShape<N> X;
+    constexpr int M = X::M, T = X::T, NH = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double2* sm = reinterpret_cast<double2*>(smraw);
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const size_t line = (size_t)blockIdx.x * X::LPC + li;
+    const double* __restrict__ ul = u + line * N;
+    double2* __restrict__ L = out + line * NH;
+    LineSmem<P> lsm{sm + li * X::PADM};
+    C v[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        const int m = j + T * s;
+        double a = ul[2 * m], b = ul[2 * m + 1];
+        if (cube) {
+            a = lam * (a * a * a);
+            b = lam * (b * b * b);
+        }
+        v[s] = cmake<double>(a, b);
+    }
+    fft<P, M, -1>(v, j, tw, 2, lsm);
+#pragma unroll
+    for (int s = 0; s < 8; s++) lsm.put(j + T * s, v[s]);
+    lsm.sync();
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        const int k = j + T * s;
+        C Z = v[s];
+        C Zp = lsm.get((M - k) & (M - 1));
+        C A = Z + conj(Zp);
+        C B = Z - conj(Zp);
+        C w = twiddle<P, -1>(tw, k);
+        C D = mul_i(cmul(w, B));
+        L[k] = make_double2(0.5 * (A.re - D.re), 0.5 * (A.im - D.im));
+        if (k == 0) L[M] = make_double2(Z.re - Z.im, 0.0);
+    }
+}
+
+// inverse C2R along x to physical lines, times scale; optionally sum u^4 (per CTA)
+template <int N>
+__global__ void __launch_bounds__(kXThreads) k_x_inverse(const double2* __restrict__ in, double* __restrict__ u,
+                                                         const double2* __restrict__ tw, double scale,
+                                                         double* __restrict__ part_sum) {
+    typedef PrecF64 P;
+    typedef cx<double> C;
+    typedef XShape<N> X;
+    constexpr int M = X::M, T = X::T, NH = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double2* sm = reinterpret_cast<double2*>(smraw);
+    __shared__ double red[96];
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const size_t line = (size_t)blockIdx.x * X::LPC + li;
+    LineSmem<P> lsm{sm + li * X::PADM};
+    C v[8];
+    x_load_c2r<P, N>(in + line * NH, j, tw, v);
+    fft<P, M, +1>(v, j, tw, 2, lsm);
+    NSum acc;
+    acc.s = 0.0;
+    acc.c = 0.0;
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        const int m = j + T * s;
+        const double a = v[s].re * scale, b = v[s].im * scale;
+        if (u) {
+            u[line * N + 2 * m] = a;
+            u[line * N + 2 * m + 1] = b;
+        }
+        if (part_sum) {
+            const double a2 = a * a, b2 = b * b;
+            acc.add(a2 * a2);
+            acc.add(b2 * b2);
+        }
+    }
+    if (part_sum) {
+        double mx = 0.0;
+        block_reduce<kXThreads>(acc, mx, red);
+        if (threadIdx.x == 0) part_sum[blockIdx.x] = acc.value();
+    }
+}
+
+// uh^{-1} = c_k uh^0 - dt vh^0 + beta_k F^0 (coef holds 2c, 2 beta); b holds vh^0 on entry
+template <int N>
+__global__ void k_startup(const double2* __restrict__ a, double2* __restrict__ b, const double2* __restrict__ f,
+                          const double2* __restrict__ coef, double dt) {
+    constexpr int NH = N / 2 + 1;
+    const size_t total = (size_t)N * N * NH;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % NH);
+        const int ky = (int)((i / NH) % N);
+        const int kz = (int)(i / ((size_t)NH * N));
+        const int my = ky <= N / 2 ? ky : ky - N, mz = kz <= N / 2 ? kz : kz - N;
+        const double2 cf = coef[kx * kx + my * my + mz * mz];
+        const double c = 0.5 * cf.x, beta = 0.5 * cf.y;
+        const double2 a0 = a[i], v0 = b[i], f0 = f[i];
+        b[i] = make_double2(c * a0.x - dt * v0.x + beta * f0.x, c * a0.y - dt * v0.y + beta * f0.y);
+    }
+}
+
+// Q(x, y) partials for arbitrary FP64 spectral pairs (energy outside the recorded steps)
+template <int N>
+__global__ void __launch_bounds__(256) k_energy_q(const double2* __restrict__ x, const double2* __restrict__ y,
+                                                  const double* __restrict__ w2tab, double inv_dt,
+                                                  double* __restrict__ part_sum) {
+    constexpr int NH = N / 2 + 1;
+    __shared__ double red[96];
+    const size_t total = (size_t)N * N * NH;
+    NSum acc;
+    acc.s = 0.0;
+    acc.c = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % NH);
+        const int ky = (int)((i / NH) % N);
+        const int kz = (int)(i / ((size_t)NH * N));
+        const int my = ky <= N / 2 ? ky : ky - N, mz = kz <= N / 2 ? kz : kz - N;
+        const double w = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
+        const double2 a = x[i], b = y[i];
+        const double dre = (a.x - b.x) * inv_dt, dim = (a.y - b.y) * inv_dt;
+        const double sre = a.x + b.x, sim = a.y + b.y;
+        acc.add(w * (0.5 * (dre * dre + dim * dim) + 0.125 * w2tab[kx * kx + my * my + mz * mz] * (sre * sre + sim * sim)));
+    }
+    double mx = 0.0;
+    block_reduce<256>(acc, mx, red);
+    if (threadIdx.x == 0) part_sum[blockIdx.x] = acc.value();
+}
+
+#ifdef KG_DEFINE_COMMON_KERNELS
+// plain Neumaier total of partials into *out (times norm)
+__global__ void __launch_bounds__(kFinThreads) k_fin_sum(const double* part_sum, int count, double norm, double* out) {
+    NSum acc;
+    double mx;
+    fin_reduce(part_sum, nullptr, count, acc, mx);
+    if (threadIdx.x == 0) *out = norm * acc.value();
+}
+
+#endif  // KG_DEFINE_COMMON_KERNELS
+
+}  // namespace kg

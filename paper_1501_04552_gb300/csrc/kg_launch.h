@@ -1,0 +1,48 @@
+// kg_launch.h -- host-side launchers of the step passes (one definition per precision).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace kg {
+
+struct KgDev;
+
+// precision ids match KG_FP64 / KG_DF64 / KG_MIXED of kg.h
+struct PassLaunch {
+    // x pass over W in the context's precision; mode 0 step, 1 peek.  Writes nparts partials.
+    cudaError_t (*pass_x)(int N, int mode, void* W, KgDev* dev, double* part_sum, double* part_max, const void* tw,
+                          double scale, double lam, cudaStream_t st);
+    // column FFT in place on W (sign -1 forward, +1 inverse)
+    cudaError_t (*col)(int N, int sign, void* W, size_t plane_stride, size_t row_stride, int nplanes, const void* tw,
+                       cudaStream_t st);
+    // inverse column FFT from an FP64 spectral source (chosen by dev->phase when src1 != NULL) into W
+    cudaError_t (*col_from_f64)(int N, const double2* src0, const double2* src1, const KgDev* dev, void* W,
+                                size_t plane_stride, size_t row_stride, int nplanes, const void* tw, cudaStream_t st);
+    // z pass with the update; writes z_parts(N) partials when recording
+    cudaError_t (*pass_z)(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum, const double2* coef,
+                          const double* w2tab, const void* tw, double inv_dt, cudaStream_t st);
+    int (*x_parts)(int N);
+    int (*z_parts)(int N);
+    size_t store_bytes;  // bytes of one complex value of W
+};
+
+extern const PassLaunch kLaunchF64;
+extern const PassLaunch kLaunchDF;
+extern const PassLaunch kLaunchF32;
+
+// FP64 set-up / read-out launchers
+cudaError_t launch_x_forward(int N, const double* u, double2* out, const double2* tw, int cube, double lam,
+                             cudaStream_t st);
+cudaError_t launch_x_inverse(int N, const double2* in, double* u, const double2* tw, double scale, double* part_sum,
+                             cudaStream_t st);
+cudaError_t launch_startup(int N, const double2* a, double2* b, const double2* f, const double2* coef, double dt,
+                           cudaStream_t st);
+cudaError_t launch_energy_q(int N, const double2* x, const double2* y, const double* w2tab, double inv_dt,
+                            double* part_sum, int nparts, cudaStream_t st);
+cudaError_t launch_fin_x(const double* ps, const double* pm, int count, KgDev* dev, double p_norm, cudaStream_t st);
+cudaError_t launch_fin_peek(const double* ps, const double* pm, int count, KgDev* dev, double p_norm,
+                            cudaStream_t st);
+cudaError_t launch_fin_z(const double* ps, int count, KgDev* dev, double q_norm, cudaStream_t st);
+cudaError_t launch_fin_sum(const double* ps, int count, double norm, double* out, cudaStream_t st);
+
+}  // namespace kg

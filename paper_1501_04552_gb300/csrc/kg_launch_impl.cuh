@@ -1,0 +1,108 @@
+// kg_launch_impl.cuh -- template launchers, instantiated once per precision.
+#pragma once
+#include "kg_kernels.cuh"
+#include "kg_launch.h"
+
+namespace kg {
+
+template <class K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define KG_DISPATCH_N(N, ...)                               \
+    switch (N) {                                            \
+        case 16: { constexpr int NN = 16; __VA_ARGS__; }    \
+        case 32: { constexpr int NN = 32; __VA_ARGS__; }    \
+        case 64: { constexpr int NN = 64; __VA_ARGS__; }    \
+        case 128: { constexpr int NN = 128; __VA_ARGS__; }  \
+        case 256: { constexpr int NN = 256; __VA_ARGS__; }  \
+        case 512: { constexpr int NN = 512; __VA_ARGS__; }  \
+        default: return cudaErrorInvalidValue;              \
+    }
+
+template <class P>
+struct Launchers {
+    typedef typename P::S S;
+
+    template <int N>
+    static cudaError_t pass_x_n(int mode, void* W, KgDev* dev, double* ps, double* pm, const void* tw, double scale,
+                                double lam, cudaStream_t st) {
+        typedef XShape<N> X;
+        const size_t smem = (size_t)X::LPC * X::PADM * sizeof(S);
+        const int grid = N * N / X::LPC;
+        if (mode == MODE_STEP) {
+            cudaError_t e = set_smem(k_pass_x<P, N, MODE_STEP>, smem);
+            if (e != cudaSuccess) return e;
+            k_pass_x<P, N, MODE_STEP><<<grid, kXThreads, smem, st>>>((S*)W, dev, ps, pm, (const S*)tw, scale, lam);
+        } else {
+            cudaError_t e = set_smem(k_pass_x<P, N, MODE_PEEK>, smem);
+            if (e != cudaSuccess) return e;
+            k_pass_x<P, N, MODE_PEEK><<<grid, kXThreads, smem, st>>>((S*)W, dev, ps, pm, (const S*)tw, scale, lam);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t pass_x(int N, int mode, void* W, KgDev* dev, double* ps, double* pm, const void* tw,
+                              double scale, double lam, cudaStream_t st) {
+        KG_DISPATCH_N(N, return pass_x_n<NN>(mode, W, dev, ps, pm, tw, scale, lam, st));
+    }
+    static int x_parts(int N) { return N * N / (kXThreads / (N / 16)); }
+
+    template <int N, int SIGN>
+    static cudaError_t col_n(void* W, size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
+        constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
+        const size_t smem = (size_t)N * C * sizeof(S);
+        auto kern = k_col<P, P, P, N, SIGN>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((NH + C - 1) / C, nplanes);
+        kern<<<grid, C * N / 8, smem, st>>>((const S*)W, (S*)W, pstride, rstride, (const S*)tw);
+        return cudaGetLastError();
+    }
+    static cudaError_t col(int N, int sign, void* W, size_t pstride, size_t rstride, int nplanes, const void* tw,
+                           cudaStream_t st) {
+        if (sign < 0) { KG_DISPATCH_N(N, return (col_n<NN, -1>(W, pstride, rstride, nplanes, tw, st))); }
+        KG_DISPATCH_N(N, return (col_n<NN, +1>(W, pstride, rstride, nplanes, tw, st)));
+    }
+
+    template <int N>
+    static cudaError_t col_from_f64_n(const double2* src0, const double2* src1, const KgDev* dev, void* W,
+                                      size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
+        constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
+        const size_t smem = (size_t)N * C * sizeof(S);
+        auto kern = k_col_sel<P, N>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((NH + C - 1) / C, nplanes);
+        kern<<<grid, C * N / 8, smem, st>>>(src0, src1, dev, (S*)W, pstride, rstride, (const S*)tw);
+        return cudaGetLastError();
+    }
+    static cudaError_t col_from_f64(int N, const double2* src0, const double2* src1, const KgDev* dev, void* W,
+                                    size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
+        KG_DISPATCH_N(N, return col_from_f64_n<NN>(src0, src1, dev, W, pstride, rstride, nplanes, tw, st));
+    }
+
+    template <int N>
+    static cudaError_t pass_z_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
+                                const double* w2, const void* tw, double inv_dt, cudaStream_t st) {
+        constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
+        const size_t smem = (size_t)N * C * sizeof(S);
+        auto kern = k_pass_z<P, N>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((NH + C - 1) / C, N);
+        kern<<<grid, C * N / 8, smem, st>>>((S*)W, S0, S1, dev, ps, coef, w2, (const S*)tw, inv_dt);
+        return cudaGetLastError();
+    }
+    static cudaError_t pass_z(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
+                              const double* w2, const void* tw, double inv_dt, cudaStream_t st) {
+        KG_DISPATCH_N(N, return pass_z_n<NN>(W, S0, S1, dev, ps, coef, w2, tw, inv_dt, st));
+    }
+    static int z_parts(int N) {
+        const int C = ColShape<P>::C, NH = N / 2 + 1;
+        return ((NH + C - 1) / C) * N;
+    }
+};
+
+}  // namespace kg

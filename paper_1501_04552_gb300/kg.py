@@ -1,0 +1,193 @@
+"""Thin ctypes binding of libkg.so (C ABI declared in include/kg.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Importing this module loads the library and raises ImportError when it
+has not been built (``python -c "import __graft_entry__ as g; g.build()"``); there
+is no fallback.  Host arrays are numpy float64 arrays [z][y][x]; device buffers may
+be passed as torch CUDA tensors or raw integer pointers.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "kg.h")
+
+KG_OK = 0
+KG_EINVAL = -1
+KG_ENOTSUP = -2
+KG_ENOMEM = -3
+KG_ECUDA = -4
+KG_ETIMEOUT = -5
+KG_EDRIFT = -6
+KG_ENOTIMPL = -7
+KG_ESTATE = -8
+
+KG_FP64 = 0
+KG_DF64 = 1
+KG_MIXED = 2
+PRECISIONS = {"fp64": KG_FP64, "df64": KG_DF64, "mixed": KG_MIXED}
+
+
+class kg_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("energy_every", C.c_int), ("nonlinearity", C.c_double),
+                ("blowup_threshold", C.c_double), ("drift_tol", C.c_double)]
+
+
+class KgError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s failed with status %d: %s" % (what, code, last_error()))
+        self.code = code
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libkg.so is not built (run paper_1501_04552_gb300/build.py); no CPU fallback exists")
+
+lib = C.CDLL(LIB_PATH)
+_vp = C.c_void_p
+_sig = {
+    "kg_init": ([C.c_int, C.c_double, C.c_double, _vp, _vp], C.c_int),
+    "kg_init_device": ([C.c_int, C.c_double, C.c_double, _vp, _vp], C.c_int),
+    "kg_step": ([C.c_int], C.c_int),
+    "kg_energy": ([C.POINTER(C.c_double)], C.c_int),
+    "kg_fetch": ([_vp], C.c_int),
+    "kg_fetch_device": ([_vp], C.c_int),
+    "kg_finalize": ([], C.c_int),
+    "kg_set_stream": ([_vp], C.c_int),
+    "kg_set_options": ([C.POINTER(kg_options)], C.c_int),
+    "kg_get_options": ([C.POINTER(kg_options)], C.c_int),
+    "kg_status": ([C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_double)],
+                  C.c_int),
+    "kg_fetch_spectral": ([_vp, _vp], C.c_int),
+    "kg_step_timed": ([C.c_int, C.POINTER(C.c_float)], C.c_int),
+    "kg_memory": ([C.POINTER(C.c_size_t)], C.c_int),
+    "kg_last_error": ([], C.c_char_p),
+}
+_state = {"N": None}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def header_symbols(path=HEADER):
+    """names of the entry points declared in include/kg.h"""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kg_[a-z_0-9]+)\s*\(", text)))
+
+
+def last_error():
+    s = lib.kg_last_error()
+    return s.decode() if s else ""
+
+
+def _check(rc, what, ok=(KG_OK,)):
+    if rc not in ok:
+        raise KgError(rc, what)
+    return rc
+
+
+def _host(a, n3, name):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n3:
+        raise ValueError("%s must hold N^3 = %d values" % (name, n3))
+    return a
+
+
+def _dptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def kg_init(N, L, dt, u0, v0=None):
+    u = _host(u0, N ** 3, "u0")
+    v = None if v0 is None else _host(v0, N ** 3, "v0")
+    _check(lib.kg_init(N, L, dt, u.ctypes.data, None if v is None else v.ctypes.data), "kg_init")
+    _state["N"] = N
+
+
+def kg_init_device(N, L, dt, d_u0, d_v0=None):
+    _check(lib.kg_init_device(N, L, dt, _dptr(d_u0), _dptr(d_v0)), "kg_init_device")
+    _state["N"] = N
+
+
+def kg_step(n=1):
+    _check(lib.kg_step(int(n)), "kg_step")
+
+
+def kg_energy(allow_drift=False):
+    E = C.c_double()
+    rc = lib.kg_energy(C.byref(E))
+    _check(rc, "kg_energy", ok=(KG_OK, KG_EDRIFT) if allow_drift else (KG_OK,))
+    return E.value
+
+
+def kg_fetch(N=None, out=None):
+    if out is None:
+        N = N or _state["N"]
+        out = np.empty((N, N, N), dtype=np.float64)
+    _check(lib.kg_fetch(out.ctypes.data), "kg_fetch")
+    return out
+
+
+def kg_fetch_device(d_u):
+    _check(lib.kg_fetch_device(_dptr(d_u)), "kg_fetch_device")
+
+
+def kg_finalize():
+    _check(lib.kg_finalize(), "kg_finalize")
+
+
+def kg_set_stream(stream):
+    ptr = stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream
+    _check(lib.kg_set_stream(ptr), "kg_set_stream")
+
+
+def kg_set_options(precision=KG_DF64, energy_every=0, nonlinearity=1.0, blowup_threshold=0.0, drift_tol=0.0):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    o = kg_options(int(precision), int(energy_every), float(nonlinearity), float(blowup_threshold), float(drift_tol))
+    _check(lib.kg_set_options(C.byref(o)), "kg_set_options")
+
+
+def kg_get_options():
+    o = kg_options()
+    _check(lib.kg_get_options(C.byref(o)), "kg_get_options")
+    return {f: getattr(o, f) for f, _ in kg_options._fields_}
+
+
+def kg_status():
+    lvl, fr, bl, mx = C.c_longlong(), C.c_int(), C.c_longlong(), C.c_double()
+    _check(lib.kg_status(C.byref(lvl), C.byref(fr), C.byref(bl), C.byref(mx)), "kg_status")
+    return {"level": lvl.value, "frozen": bool(fr.value), "blowup_level": bl.value, "maxabs": mx.value}
+
+
+def kg_fetch_spectral(N):
+    a = np.empty((N, N, N // 2 + 1), dtype=np.complex128)
+    b = np.empty_like(a)
+    _check(lib.kg_fetch_spectral(a.ctypes.data, b.ctypes.data), "kg_fetch_spectral")
+    return a, b
+
+
+def kg_step_timed(n):
+    ms = (C.c_float * 4)()
+    _check(lib.kg_step_timed(int(n), ms), "kg_step_timed")
+    return [ms[i] for i in range(4)]
+
+
+def kg_memory():
+    b = C.c_size_t()
+    _check(lib.kg_memory(C.byref(b)), "kg_memory")
+    return b.value
+
+
+def kg_last_error():
+    return last_error()
+
