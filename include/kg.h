@@ -116,6 +116,28 @@ int kg_step_timed(int n, float* ms);
 /* Bytes of device memory the context holds. */
 int kg_memory(size_t* bytes);
 
+/* Quadratic energy Q of a caller-held Fourier state pair, without allocating.
+ * The paper has no counterpart: this is a service for callers that cannot call
+ * cudaMalloc, such as applications whose device memory belongs to another
+ * allocator or to a pool fixed at start-up, and loops that cannot take the device
+ * synchronisation of cudaMalloc/cudaFree.
+ *   d_cur, d_old  device arrays of N*N*(N/2+1) complex doubles (interleaved re/im,
+ *                 [kz][ky][kx]) holding uh^n and uh^{n-1}; read only
+ *   d_Q           device double that receives Q^{n-1/2} as defined above
+ *                 (the energy of the state pair when lam = 0)
+ *   stream        cudaStream_t to enqueue on (NULL: the legacy default stream)
+ * Needs no context.  The partial sums go to a static device array of 8192 doubles
+ * (64 KiB, held by every GPU that loads the library until the process exits),
+ * which bounds the size: N must be even with N*N*(N/2+1) <= 8192*16384 modes
+ * (N <= 644); larger or odd N returns KG_ENOTSUP.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls on a device
+ * share the array, so calls that overlap on the GPU (concurrent streams) race.
+ * Enqueued asynchronously; allocates nothing.  Errors: KG_ENOTSUP, KG_EINVAL
+ * (NULL pointer, L or dt not finite and > 0), KG_ECUDA. */
+int kg_energy_q_noalloc(int N, double L, double dt, const double* d_cur, const double* d_old, double* d_Q,
+                        void* stream);
+
 /* Description of the last failure in this thread ("" if none). */
 const char* kg_last_error(void);
 

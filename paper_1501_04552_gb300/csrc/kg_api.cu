@@ -365,6 +365,11 @@ int p_from_state(Ctx* c, bool older, double* out) {
 
 }  // namespace
 
+namespace kg {
+// lets other translation units of the library report through kg_last_error()
+int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace kg
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

@@ -65,6 +65,7 @@ _sig = {
     "kg_step_timed": ([C.c_int, C.POINTER(C.c_float)], C.c_int),
     "kg_memory": ([C.POINTER(C.c_size_t)], C.c_int),
     "kg_last_error": ([], C.c_char_p),
+    "kg_energy_q_noalloc": ([C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp], C.c_int),
 }
 _state = {"N": None}
 for _name, (_args, _res) in _sig.items():
