@@ -35,11 +35,12 @@ METRIC = "512^3 KG steps/s"
 S_BYTES = N_GRID * N_GRID * (N_GRID // 2 + 1) * 16      # one complex128 half-spectrum array
 
 
-def algorithmic_bytes(prec):
+def algorithmic_bytes(prec, n=N_GRID):
     """bytes an ideal step moves: 4 passes reading and writing W, plus reading uh^n,
     uh^{n-1} and writing uh^{n+1} (FP64) in the z pass"""
-    w = S_BYTES if prec in ("fp64", "df64") else S_BYTES // 2
-    per_pass = {"x": 2 * w, "yf": 2 * w, "z": 2 * w + 3 * S_BYTES, "yi": 2 * w}
+    s_bytes = n * n * (n // 2 + 1) * 16
+    w = s_bytes if prec in ("fp64", "df64") else s_bytes // 2
+    per_pass = {"x": 2 * w, "yf": 2 * w, "z": 2 * w + 3 * s_bytes, "yi": 2 * w}
     return per_pass, sum(per_pass.values())
 
 
@@ -158,6 +159,8 @@ def main():
     ap.add_argument("--precision", default=PRECISION, choices=["fp64", "df64", "mixed"])
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-extras", action="store_true", help="skip the other precisions and the cuFFT point")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle sample (profiling runs)")
+    ap.add_argument("--grid", type=int, default=N_GRID, help="grid size (512 is the benchmark; smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         args.steps = min(args.steps, 3)
@@ -179,7 +182,8 @@ def main():
     from paper_1501_04552_gb300 import inputs as I
     from paper_1501_04552_gb300 import kg
 
-    w = I.bump_noise(N_GRID)
+    NG = args.grid
+    w = I.bump_noise(NG)
     u0 = w["u0"]
     stream = torch.cuda.Stream()
     kg.kg_set_stream(stream)
@@ -191,7 +195,7 @@ def main():
     def timed_steps(prec, steps, warmup):
         kg.kg_set_options(precision=prec, energy_every=ENERGY_EVERY)
         d_u0 = torch.from_numpy(u0).to(f"cuda:{local}")
-        kg.kg_init_device(N_GRID, L_BOX, DT, d_u0, None)
+        kg.kg_init_device(NG, L_BOX, DT, d_u0, None)
         del d_u0
         kg.kg_step(warmup)
         stream.synchronize()
@@ -221,7 +225,7 @@ def main():
     # per-pass device times (CUDA events on the library's stream) for the roofline
     pass_ms = kg.kg_step_timed(args.steps)
     pass_avg = [t / args.steps for t in pass_ms]
-    per_pass_bytes, step_bytes = algorithmic_bytes(prec)
+    per_pass_bytes, step_bytes = algorithmic_bytes(prec, NG)
     names = ["x", "yf", "z", "yi"]
     dom = int(np.argmax(pass_avg))
     peak, peak_kind = peaks()
@@ -235,12 +239,12 @@ def main():
 
     # end to end through the public API with host buffers: pinned u0 -> kg_init, K steps, kg_fetch -> host
     pinned_u0 = torch.from_numpy(u0).pin_memory()
-    out = torch.empty((N_GRID,) * 3, dtype=torch.float64).pin_memory()
+    out = torch.empty((NG,) * 3, dtype=torch.float64).pin_memory()
     kg.kg_set_options(precision=prec, energy_every=ENERGY_EVERY)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    kg.lib.kg_init(N_GRID, L_BOX, DT, pinned_u0.data_ptr(), None)
+    kg.lib.kg_init(NG, L_BOX, DT, pinned_u0.data_ptr(), None)
     kg.kg_step(args.steps)
     kg.lib.kg_fetch(out.data_ptr())
     torch.cuda.synchronize()
@@ -264,7 +268,7 @@ def main():
         extras["cufft_torch"] = torch_fft_point(u0, local)
 
     base = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         base = cpu_baseline(w, args.cpu_sample_steps)
 
     kg.kg_finalize()
@@ -275,7 +279,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "df64": "f64 state+update, df64 FFT",
                                                                   "mixed": "f64 state+update, f32 FFT"}[prec],
                 "data": "synthetic",
-                "config": {"workload": "kg512_bump_noise", "N": N_GRID, "L": L_BOX, "dt": DT, "seed": 1501,
+                "config": {"workload": "kg%d_bump_noise" % NG, "N": NG, "L": L_BOX, "dt": DT, "seed": 1501,
                            "precision": prec, "energy_every": ENERGY_EVERY, "parallelism": "replicas",
                            "l2": "inputs larger than L2 (each state array 1.08 GB)"},
                 "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "clocks": clocks,
