@@ -116,6 +116,42 @@ int kg_step_timed(int n, float* ms);
 /* Bytes of device memory the context holds. */
 int kg_memory(size_t* bytes);
 
+/* ---- batched parametric ensemble (blow-up studies, section 1 of the paper) ----
+ * count independent instances (1..1024) on grids Ns[i] in {64, 128}, side L, step dt,
+ * u0 = A[i] exp(-|x|^2 / s[i]^2), v0 = 0, in the precision and nonlinearity of the
+ * current options.  Each time step of the whole ensemble is one persistent
+ * cooperative kernel launch (four passes separated by bounded grid barriers), and
+ * runs of steps are replayed from a captured CUDA graph.  One ensemble per process;
+ * independent of the kg_init context.  Errors: KG_EINVAL, KG_ENOTSUP, KG_ENOMEM,
+ * KG_ECUDA, KG_ETIMEOUT (a grid barrier wait gave up; the ensemble state is then
+ * undefined and must be re-initialised). */
+int kg_ens_init(int count, const int* Ns, double L, double dt, const double* A, const double* s);
+
+/* Advance every instance that has not blown up by up to max_steps steps.  With
+ * threshold > 0 an instance whose max|u^n| exceeds it is frozen at level n (its
+ * blow-up level); the run ends early once all instances are frozen.  *steps_done
+ * receives the number of ensemble steps launched and *ms their device time (either
+ * pointer may be NULL).  Synchronises. */
+int kg_ens_run(int max_steps, double threshold, long long* steps_done, double* ms);
+
+/* Per-instance results (arrays of count entries, any may be NULL): frozen flag,
+ * blow-up level (-1 if none), current level, max|u| seen by its last step. */
+int kg_ens_results(int* frozen, long long* blowup_level, long long* level, double* maxabs);
+
+/* Low-mode shell energies of uh^0, count x 4 doubles: (h^3/N^3) sum w_k omega_k^2 |uh_k|^2 / 2
+ * over integer wavenumber norms |m| in {0}, (0,1], (1,2], (2,4]. */
+int kg_ens_features(double* shells);
+
+/* u^n of instance i (N^3 doubles, host memory). */
+int kg_ens_fetch(int i, double* u);
+
+/* Time every launch shape (CTAs per SM x unit order) for `steps` steps on the current
+ * ensemble, keep the fastest, and remember it for later kg_ens_init calls with the
+ * same precision and grid mix.  Advances the ensemble. */
+int kg_ens_tune(int steps, int* blocks_per_sm, int* order);
+
+int kg_ens_finalize(void);
+
 /* Quadratic energy Q of a caller-held Fourier state pair, without allocating.
  * The paper has no counterpart: this is a service for callers that cannot call
  * cudaMalloc, such as applications whose device memory belongs to another

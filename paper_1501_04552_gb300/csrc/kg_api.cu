@@ -35,18 +35,10 @@ int fail(int code, const std::string& msg) {
         if (e_ != cudaSuccess) return fail(KG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-const double kPi = 3.14159265358979323846;
 
 bool supported_n(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256 || N == 512; }
 
-const PassLaunch* launcher(int prec) {
-    switch (prec) {
-        case KG_FP64: return &kLaunchF64;
-        case KG_DF64: return &kLaunchDF;
-        case KG_MIXED: return &kLaunchF32;
-        default: return nullptr;
-    }
-}
+const PassLaunch* launcher(int prec) { return launcher_for(prec); }
 
 // Test hook: KG_TEST_FAIL_ALLOC=k makes the k-th device allocation of a set-up fail
 // (counted from 1), so the error path and its clean-up can be exercised on the host.
@@ -115,54 +107,15 @@ void destroy(Ctx* c) {
     delete c;
 }
 
-// host tables -------------------------------------------------------------
 int upload_tables(Ctx* c) {
-    const int N = c->N;
-    std::vector<double2> t64(N);
-    for (int j = 0; j < N; j++) {
-        const double a = 2.0 * kPi * (double)j / (double)N;
-        t64[j] = make_double2(std::cos(a), -std::sin(a));
-    }
-    int rc = dalloc(c, (void**)&c->tw64, sizeof(double2) * N, "twiddles fp64");
+    Tables t;
+    int rc = make_tables(c->N, c->prec, c->L, c->dt,
+                         [c](void** p, size_t b, const char* w) { return dalloc(c, p, b, w); }, &t);
     if (rc) return rc;
-    KG_CK(cudaMemcpy(c->tw64, t64.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
-    if (c->prec == KG_FP64) {
-        c->tw = c->tw64;
-    } else if (c->prec == KG_DF64) {
-        std::vector<float4> t(N);
-        for (int j = 0; j < N; j++) {
-            float rh = (float)t64[j].x, ih = (float)t64[j].y;
-            t[j] = make_float4(rh, (float)(t64[j].x - (double)rh), ih, (float)(t64[j].y - (double)ih));
-        }
-        rc = dalloc(c, &c->tw, sizeof(float4) * N, "twiddles df");
-        if (rc) return rc;
-        KG_CK(cudaMemcpy(c->tw, t.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
-    } else {
-        std::vector<float2> t(N);
-        for (int j = 0; j < N; j++) t[j] = make_float2((float)t64[j].x, (float)t64[j].y);
-        rc = dalloc(c, &c->tw, sizeof(float2) * N, "twiddles f32");
-        if (rc) return rc;
-        KG_CK(cudaMemcpy(c->tw, t.data(), sizeof(float2) * N, cudaMemcpyHostToDevice));
-    }
-    // coefficients of Eq. (2) by integer wavenumber norm m^2 = mx^2 + my^2 + mz^2
-    const int m2max = 3 * (N / 2) * (N / 2);
-    std::vector<double2> cf(m2max + 1);
-    std::vector<double> w2(m2max + 1);
-    const double kf = 2.0 * kPi / c->L;
-    for (int m2 = 0; m2 <= m2max; m2++) {
-        const double om2 = 1.0 + kf * kf * (double)m2;
-        const double a = c->dt * c->dt * om2 / 4.0;
-        const double cc = (1.0 - a) / (1.0 + a);
-        const double beta = (c->dt * c->dt / 2.0) / (1.0 + a);
-        cf[m2] = make_double2(2.0 * cc, 2.0 * beta);
-        w2[m2] = om2;
-    }
-    rc = dalloc(c, (void**)&c->coef, sizeof(double2) * (m2max + 1), "coefficients");
-    if (rc) return rc;
-    rc = dalloc(c, (void**)&c->w2, sizeof(double) * (m2max + 1), "omega^2");
-    if (rc) return rc;
-    KG_CK(cudaMemcpy(c->coef, cf.data(), sizeof(double2) * (m2max + 1), cudaMemcpyHostToDevice));
-    KG_CK(cudaMemcpy(c->w2, w2.data(), sizeof(double) * (m2max + 1), cudaMemcpyHostToDevice));
+    c->tw = t.tw;
+    c->tw64 = t.tw64;
+    c->coef = t.coef;
+    c->w2 = t.w2;
     return KG_OK;
 }
 
@@ -171,16 +124,6 @@ int ensure_scratch(Ctx* c) {
     if (!c->tmp) rc = dalloc(c, (void**)&c->tmp, sizeof(double2) * c->nspec, "fp64 spectral scratch");
     if (!rc && !c->phys) rc = dalloc(c, (void**)&c->phys, sizeof(double) * c->nphys, "physical scratch");
     return rc;
-}
-
-// FP64 R2C of a physical device array into out (cube: lam u^3 instead of u)
-int forward3d(Ctx* c, const double* u, double2* out, int cube) {
-    const int N = c->N, NH = c->NH;
-    cudaStream_t st = stream_of(c);
-    KG_CK(launch_x_forward(N, u, out, c->tw64, cube, c->lam, st));
-    KG_CK(kLaunchF64.col(N, -1, out, (size_t)N * NH, NH, N, c->tw64, st));   // y
-    KG_CK(kLaunchF64.col(N, -1, out, NH, (size_t)N * NH, N, c->tw64, st));   // z
-    return KG_OK;
 }
 
 // FP64 inverse of a spectral state array (phase-selected pair) into c->tmp (yz only)
@@ -257,8 +200,7 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
     }
 
     cudaStream_t st = stream_of(c);
-    const int NH = c->NH;
-    // F^0 = R2C(lam u0^3) into W viewed as FP64 when it is large enough, else into tmp
+    // F^0 = R2C(lam u0^3) goes to W viewed as FP64 when it is large enough, else to a set-up scratch
     double2* fbuf = nullptr;
     double2* extra = nullptr;
     if (c->pl->store_bytes == sizeof(double2)) {
@@ -267,24 +209,13 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
         KG_TRY(dalloc(c, (void**)&extra, sizeof(double2) * c->nspec, "set-up scratch"));
         fbuf = extra;
     }
-    auto copy_in = [&](const double* src) -> int {
-        KG_CK(cudaMemcpyAsync(c->phys, src, sizeof(double) * n3, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        return KG_OK;
-    };
-    KG_TRY(copy_in(u0));
-    KG_TRY(forward3d(c, c->phys, fbuf, 1));    // F^0
-    KG_TRY(forward3d(c, c->phys, c->S0, 0));   // uh^0
-    if (v0) {
-        KG_TRY(copy_in(v0));
-        KG_TRY(forward3d(c, c->phys, c->S1, 0));   // vh^0
-    } else {
-        if (cudaMemsetAsync(c->S1, 0, sizeof(double2) * c->nspec, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "memset"));
+    {
+        cudaError_t e = cudaMemcpyAsync(c->phys, u0, sizeof(double) * n3,
+                                        device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) KG_TRY(fail(KG_ECUDA, std::string("copy u0: ") + cudaGetErrorString(e)));
     }
-    if (launch_startup(N, c->S0, c->S1, fbuf, c->coef, dt, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "startup launch"));
-    // W <- yz-inverse of uh^0, in the pass precision
-    if (c->pl->col_from_f64(N, c->S0, c->S1, nullptr, c->W, NH, (size_t)N * NH, N, c->tw, st) != cudaSuccess)
-        KG_TRY(fail(KG_ECUDA, "init z inverse"));
-    if (c->pl->col(N, +1, c->W, (size_t)N * NH, NH, N, c->tw, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "init y inverse"));
+    Tables tb{c->tw, c->tw64, c->coef, c->w2};
+    KG_TRY(init_state(N, c->prec, dt, c->lam, tb, c->phys, v0, device_ptrs, c->S0, c->S1, c->W, fbuf, st));
     KgDev d;
     std::memset(&d, 0, sizeof(d));
     d.level = 0;

@@ -1,0 +1,492 @@
+// kg_ensemble.cu -- C ABI of the batched parametric ensemble (kg_ens_*).
+//
+// Many independent instances of the scheme of section 1.1.2 (Eq. (2)) on 64^3 and
+// 128^3 grids, initial data u0 = A exp(-|x|^2 / s^2), v0 = 0 (the parametric blow-up
+// studies of section 1), advanced together: each time step is one persistent
+// cooperative launch (k_ens_step), and runs of steps are replayed from a captured
+// CUDA graph.  Launch shape (CTAs per SM, unit visiting order) comes from a small
+// autotuner that times the candidates on the actual ensemble.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/kg.h"
+#include "kg_ensemble.cuh"
+#include "kg_launch.h"
+
+using namespace kg;
+
+namespace {
+
+constexpr int kGraphSteps = 10;
+
+// launch shape chosen by kg_ens_tune, reused by later kg_ens_init calls with the
+// same precision and the same numbers of 64^3 and 128^3 instances
+struct Tuned {
+    bool valid = false;
+    int prec = 0, n64 = 0, n128 = 0, bps = 2, order = 1;
+};
+Tuned g_tuned;
+
+void count_sizes(const std::vector<int>& Ns, int* n64, int* n128) {
+    *n64 = 0;
+    *n128 = 0;
+    for (int n : Ns) (n == 64 ? *n64 : *n128) += 1;
+}
+
+int efail(int code, const std::string& msg) { return set_last_error(code, msg); }
+
+#define KG_ECK(call)                                                                               \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return efail(KG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// u = A exp(-|x|^2 / s^2) on the N^3 grid x_j = -L/2 + j L/N (an initial field, not the method)
+__global__ void k_gaussian(double* u, int N, double L, double A, double s) {
+    const size_t n3 = (size_t)N * N * N;
+    const double h = L / N, inv_s2 = 1.0 / (s * s);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((size_t)N * N));
+        const double px = -L / 2 + h * x, py = -L / 2 + h * y, pz = -L / 2 + h * z;
+        u[i] = A * exp(-(px * px + py * py + pz * pz) * inv_s2);
+    }
+}
+
+// low-mode shell energies of uh^0: (h^3/N^3) sum_{shell} w_k omega_k^2 |uh_k|^2 / 2,
+// shells |m| in {0}, (0,1], (1,2], (2,4]; one CTA, one instance
+__global__ void k_shells(const double2* __restrict__ uh, int N, double L, double* __restrict__ out4) {
+    __shared__ double acc[4][256];
+    const int NH = N / 2 + 1;
+    double loc[4] = {0, 0, 0, 0};
+    const double kf = 2.0 * 3.14159265358979323846 / L;
+    for (int t = threadIdx.x; t < 9 * 9 * 5; t += blockDim.x) {   // |m| <= 4 box, kx >= 0
+        const int mx = t % 5, my = (t / 5) % 9 - 4, mz = t / 45 - 4;
+        const int m2 = mx * mx + my * my + mz * mz;
+        const int sh = (m2 == 0) ? 0 : (m2 <= 1) ? 1 : (m2 <= 4) ? 2 : (m2 <= 16) ? 3 : -1;
+        if (sh < 0) continue;
+        const int ky = (my + N) % N, kz = (mz + N) % N;
+        const double2 v = uh[((size_t)kz * N + ky) * NH + mx];
+        const double w = (mx == 0 || mx == N / 2) ? 1.0 : 2.0;
+        loc[sh] += w * 0.5 * (1.0 + kf * kf * m2) * (v.x * v.x + v.y * v.y);
+    }
+    for (int q = 0; q < 4; q++) acc[q][threadIdx.x] = loc[q];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int i = 0; i < 256; i++) s += acc[threadIdx.x][i];
+        const double h = L / N;
+        out4[threadIdx.x] = s * h * h * h / ((double)N * N * N);
+    }
+}
+
+struct Ens {
+    int count = 0, prec = KG_DF64;
+    double L = 0, dt = 0, lam = 1.0;
+    std::vector<int> Ns;
+    Tables tab[2];              // [0]: 64^3, [1]: 128^3
+    bool have[2] = {false, false};
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    std::vector<EnsInst> h_inst;
+    EnsInst* d_inst = nullptr;
+    unsigned* d_maxkey = nullptr;
+    unsigned* d_bar = nullptr;
+    int* d_status = nullptr;
+    unsigned long long* d_step = nullptr;
+    int* d_order = nullptr;
+    double* d_feat = nullptr;
+    double2* tmp = nullptr;     // FP64 spectral scratch of the largest grid
+    double* phys = nullptr;     // physical scratch of the largest grid
+    cudaStream_t stream = nullptr;
+    const PassLaunch* pl = nullptr;
+    int bps = 1, grid = 0, order = 0, nsm = 0;
+    double threshold = -1.0;
+    int missing = 0;
+    long long spin_limit = 1ll << 24;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+Ens* g_ens = nullptr;
+
+int ealloc(Ens* e, void** p, size_t bytes, const char* what) {
+    cudaError_t r = cudaMalloc(p, bytes);
+    if (r != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return efail(KG_ENOMEM, std::string("cudaMalloc(") + what + "): " + cudaGetErrorString(r));
+    }
+    e->allocs.push_back(*p);
+    e->bytes += bytes;
+    return KG_OK;
+}
+
+void ens_destroy(Ens* e) {
+    if (!e) return;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    for (void* p : e->allocs) cudaFree(p);
+    if (e->ev0) cudaEventDestroy(e->ev0);
+    if (e->ev1) cudaEventDestroy(e->ev1);
+    if (e->stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+unsigned threshold_key(double thr) {
+    if (!(thr > 0.0)) return 0xFFFFFFFFu;
+    float f = (float)thr;
+    unsigned k;
+    std::memcpy(&k, &f, 4);
+    return k;
+}
+
+EnsParams make_params(const Ens* e) {
+    EnsParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.inst = e->d_inst;
+    p.count = e->count;
+    p.order = e->order;
+    for (int t = 0; t < 2; t++) {
+        EnsTab& tb = t == 0 ? p.tab64 : p.tab128;
+        if (e->have[t]) {
+            tb.tw = e->tab[t].tw;
+            tb.coef = e->tab[t].coef;
+            tb.w2 = e->tab[t].w2;
+        }
+    }
+    p.maxkey = e->d_maxkey;
+    p.bar = e->d_bar;
+    p.status = e->d_status;
+    p.step_ctr = e->d_step;
+    p.order_idx = e->d_order;
+    p.lam = e->lam;
+    p.inv_dt = 1.0 / e->dt;
+    p.thr_key = threshold_key(e->threshold);
+    p.missing = e->missing;
+    p.spin_limit = e->spin_limit;
+    return p;
+}
+
+int upload_order(Ens* e) {
+    std::vector<int> idx(e->count);
+    for (int i = 0; i < e->count; i++) idx[i] = i;
+    if (e->order == 1)   // larger grids first
+        std::stable_sort(idx.begin(), idx.end(), [e](int a, int b) { return e->Ns[a] > e->Ns[b]; });
+    KG_ECK(cudaMemcpy(e->d_order, idx.data(), sizeof(int) * e->count, cudaMemcpyHostToDevice));
+    return KG_OK;
+}
+
+int rebuild_graph(Ens* e) {
+    if (e->gexec) {
+        cudaGraphExecDestroy(e->gexec);
+        e->gexec = nullptr;
+    }
+    const EnsParams p = make_params(e);
+    cudaGraph_t g = nullptr;
+    KG_ECK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int s = 0; s < kGraphSteps && le == cudaSuccess; s++) le = e->pl->ens_step(p, e->grid, e->stream);
+    cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return efail(KG_ECUDA, std::string("ensemble graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ce));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&e->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return efail(KG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    return KG_OK;
+}
+
+int check_status(Ens* e) {
+    int st = 0;
+    KG_ECK(cudaMemcpy(&st, e->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) return efail(KG_ETIMEOUT, "ensemble grid barrier wait timed out");
+    return KG_OK;
+}
+
+int set_shape(Ens* e, int bps, int order) {
+    const int maxb = e->pl->ens_blocks_per_sm();
+    if (maxb < 1) return efail(KG_ECUDA, "ensemble kernel cannot be resident (occupancy 0)");
+    e->bps = std::max(1, std::min(bps, maxb));
+    e->grid = e->bps * e->nsm;
+    e->order = order;
+    int rc = upload_order(e);
+    if (!rc) rc = rebuild_graph(e);
+    return rc;
+}
+
+// one run of n steps without the graph (used for remainders and by the tuner)
+int launch_steps(Ens* e, int n) {
+    const EnsParams p = make_params(e);
+    for (int s = 0; s < n; s++) KG_ECK(e->pl->ens_step(p, e->grid, e->stream));
+    return KG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kg_ens_init(int count, const int* Ns, double L, double dt, const double* A, const double* s) {
+    if (count < 1 || count > kEnsMaxInst) return efail(KG_EINVAL, "count must be in [1, 1024]");
+    if (!Ns || !A || !s) return efail(KG_EINVAL, "NULL argument");
+    if (!(L > 0.0) || !std::isfinite(L) || !(dt > 0.0) || !std::isfinite(dt))
+        return efail(KG_EINVAL, "L and dt must be finite and > 0");
+    for (int i = 0; i < count; i++) {
+        if (Ns[i] != 64 && Ns[i] != 128) return efail(KG_ENOTSUP, "ensemble grids must be 64 or 128");
+        if (!std::isfinite(A[i]) || !(s[i] > 0.0) || !std::isfinite(s[i])) return efail(KG_EINVAL, "bad A or s");
+    }
+    kg_options opt;
+    kg_get_options(&opt);
+    if (g_ens) {
+        ens_destroy(g_ens);
+        g_ens = nullptr;
+    }
+    Ens* e = new Ens();
+    e->count = count;
+    e->prec = opt.precision;
+    e->pl = launcher_for(e->prec);
+    e->L = L;
+    e->dt = dt;
+    e->lam = opt.nonlinearity;
+    e->Ns.assign(Ns, Ns + count);
+    const char* miss = std::getenv("KG_TEST_ENS_MISSING_CTA");   // test hook: force a barrier timeout
+    if (miss && std::atoi(miss) == 1) {
+        e->missing = 1;
+        e->spin_limit = 1ll << 16;
+    }
+    int rc = KG_OK;
+#define KG_ETRY(x)          \
+    do {                    \
+        rc = (x);           \
+        if (rc) {           \
+            ens_destroy(e); \
+            return rc;      \
+        }                   \
+    } while (0)
+    {
+        cudaError_t r = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+        if (r != cudaSuccess) KG_ETRY(efail(KG_ECUDA, "cudaStreamCreate"));
+        if (cudaEventCreate(&e->ev0) != cudaSuccess || cudaEventCreate(&e->ev1) != cudaSuccess)
+            KG_ETRY(efail(KG_ECUDA, "cudaEventCreate"));
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&e->nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    auto alloc = [e](void** p, size_t b, const char* w) { return ealloc(e, p, b, w); };
+    int nmax = 0;
+    for (int i = 0; i < count; i++) {
+        const int t = Ns[i] == 64 ? 0 : 1;
+        nmax = std::max(nmax, Ns[i]);
+        if (!e->have[t]) {
+            KG_ETRY(make_tables(Ns[i], e->prec, L, dt, alloc, &e->tab[t]));
+            e->have[t] = true;
+        }
+    }
+    const size_t spec_max = (size_t)nmax * nmax * (nmax / 2 + 1);
+    KG_ETRY(ealloc(e, (void**)&e->tmp, sizeof(double2) * spec_max, "ensemble spectral scratch"));
+    KG_ETRY(ealloc(e, (void**)&e->phys, sizeof(double) * (size_t)nmax * nmax * nmax, "ensemble physical scratch"));
+    // one allocation per array class, instances at 256-byte aligned offsets
+    size_t off_s = 0, off_w = 0;
+    std::vector<size_t> os(count), ow(count);
+    for (int i = 0; i < count; i++) {
+        const size_t ns = (size_t)Ns[i] * Ns[i] * (Ns[i] / 2 + 1);
+        os[i] = off_s;
+        ow[i] = off_w;
+        off_s += (ns * sizeof(double2) + 255) & ~(size_t)255;
+        off_w += (ns * e->pl->store_bytes + 255) & ~(size_t)255;
+    }
+    char *b0 = nullptr, *b1 = nullptr, *bw = nullptr;
+    KG_ETRY(ealloc(e, (void**)&b0, off_s, "ensemble S0"));
+    KG_ETRY(ealloc(e, (void**)&b1, off_s, "ensemble S1"));
+    KG_ETRY(ealloc(e, (void**)&bw, off_w, "ensemble W"));
+    KG_ETRY(ealloc(e, (void**)&e->d_inst, sizeof(EnsInst) * count, "ensemble descriptors"));
+    KG_ETRY(ealloc(e, (void**)&e->d_maxkey, sizeof(unsigned) * 2 * count, "ensemble max keys"));
+    KG_ETRY(ealloc(e, (void**)&e->d_bar, sizeof(unsigned) * 2, "ensemble barrier"));
+    KG_ETRY(ealloc(e, (void**)&e->d_status, sizeof(int), "ensemble status"));
+    KG_ETRY(ealloc(e, (void**)&e->d_step, sizeof(unsigned long long), "ensemble step counter"));
+    KG_ETRY(ealloc(e, (void**)&e->d_order, sizeof(int) * count, "ensemble order"));
+    KG_ETRY(ealloc(e, (void**)&e->d_feat, sizeof(double) * 4 * count, "ensemble features"));
+    e->h_inst.resize(count);
+    for (int i = 0; i < count; i++) {
+        const int N = Ns[i];
+        const int t = N == 64 ? 0 : 1;
+        EnsInst& in = e->h_inst[i];
+        std::memset(&in, 0, sizeof(in));
+        in.S0 = (double2*)(b0 + os[i]);
+        in.S1 = (double2*)(b1 + os[i]);
+        in.W = (void*)(bw + ow[i]);
+        in.N = N;
+        in.blowup_level = -1;
+        k_gaussian<<<152 * 4, 256, 0, e->stream>>>(e->phys, N, L, A[i], s[i]);
+        if (cudaGetLastError() != cudaSuccess) KG_ETRY(efail(KG_ECUDA, "gaussian launch"));
+        // F^0 scratch: W itself when it holds 16-byte values, else the spectral scratch
+        double2* fbuf = e->pl->store_bytes == sizeof(double2) ? (double2*)in.W : e->tmp;
+        KG_ETRY(init_state(N, e->prec, dt, e->lam, e->tab[t], e->phys, nullptr, false, in.S0, in.S1, in.W, fbuf,
+                           e->stream));
+        k_shells<<<1, 256, 0, e->stream>>>(in.S0, N, L, e->d_feat + 4 * i);
+        if (cudaGetLastError() != cudaSuccess) KG_ETRY(efail(KG_ECUDA, "shells launch"));
+    }
+    if (cudaMemcpyAsync(e->d_inst, e->h_inst.data(), sizeof(EnsInst) * count, cudaMemcpyHostToDevice, e->stream) != cudaSuccess ||
+        cudaMemsetAsync(e->d_maxkey, 0, sizeof(unsigned) * 2 * count, e->stream) != cudaSuccess ||
+        cudaMemsetAsync(e->d_bar, 0, sizeof(unsigned) * 2, e->stream) != cudaSuccess ||
+        cudaMemsetAsync(e->d_status, 0, sizeof(int), e->stream) != cudaSuccess ||
+        cudaMemsetAsync(e->d_step, 0, sizeof(unsigned long long), e->stream) != cudaSuccess)
+        KG_ETRY(efail(KG_ECUDA, "ensemble state upload"));
+    if (cudaStreamSynchronize(e->stream) != cudaSuccess) KG_ETRY(efail(KG_ECUDA, "ensemble init"));
+    e->threshold = -1.0;
+    {
+        int n64, n128;
+        count_sizes(e->Ns, &n64, &n128);
+        const bool use = g_tuned.valid && g_tuned.prec == e->prec && g_tuned.n64 == n64 && g_tuned.n128 == n128;
+        KG_ETRY(set_shape(e, use ? g_tuned.bps : 2, use ? g_tuned.order : 1));
+    }
+#undef KG_ETRY
+    g_ens = e;
+    return KG_OK;
+}
+
+int kg_ens_run(int max_steps, double threshold, long long* steps_done, double* ms) {
+    Ens* e = g_ens;
+    if (!e) return efail(KG_ESTATE, "kg_ens_run before kg_ens_init");
+    if (max_steps < 0 || !std::isfinite(threshold)) return efail(KG_EINVAL, "bad arguments");
+    if (threshold != e->threshold) {
+        e->threshold = threshold;
+        int rc = rebuild_graph(e);
+        if (rc) return rc;
+    }
+    long long done = 0;
+    KG_ECK(cudaEventRecord(e->ev0, e->stream));
+    const int check_every = 5 * kGraphSteps;
+    while (done < max_steps) {
+        const long long left = max_steps - done;
+        if (left >= kGraphSteps) {
+            KG_ECK(cudaGraphLaunch(e->gexec, e->stream));
+            done += kGraphSteps;
+        } else {
+            int rc = launch_steps(e, (int)left);
+            if (rc) return rc;
+            done += left;
+        }
+        if (done % check_every == 0 || done >= max_steps) {
+            // stop early once every instance has blown up
+            KG_ECK(cudaMemcpyAsync(e->h_inst.data(), e->d_inst, sizeof(EnsInst) * e->count, cudaMemcpyDeviceToHost,
+                                   e->stream));
+            KG_ECK(cudaStreamSynchronize(e->stream));
+            int rc = check_status(e);
+            if (rc) return rc;
+            bool any = false;
+            for (const EnsInst& in : e->h_inst) any = any || !in.frozen;
+            if (!any) break;
+        }
+    }
+    KG_ECK(cudaEventRecord(e->ev1, e->stream));
+    KG_ECK(cudaEventSynchronize(e->ev1));
+    int rc = check_status(e);
+    if (rc) return rc;
+    float t = 0.f;
+    KG_ECK(cudaEventElapsedTime(&t, e->ev0, e->ev1));
+    if (steps_done) *steps_done = done;
+    if (ms) *ms = t;
+    return KG_OK;
+}
+
+int kg_ens_results(int* frozen, long long* blowup_level, long long* level, double* maxabs) {
+    Ens* e = g_ens;
+    if (!e) return efail(KG_ESTATE, "kg_ens_results before kg_ens_init");
+    KG_ECK(cudaStreamSynchronize(e->stream));
+    KG_ECK(cudaMemcpy(e->h_inst.data(), e->d_inst, sizeof(EnsInst) * e->count, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < e->count; i++) {
+        const EnsInst& in = e->h_inst[i];
+        if (frozen) frozen[i] = in.frozen;
+        if (blowup_level) blowup_level[i] = in.blowup_level;
+        if (level) level[i] = in.level;
+        if (maxabs) maxabs[i] = in.maxabs;
+    }
+    return KG_OK;
+}
+
+int kg_ens_features(double* shells) {
+    Ens* e = g_ens;
+    if (!e) return efail(KG_ESTATE, "kg_ens_features before kg_ens_init");
+    if (!shells) return efail(KG_EINVAL, "NULL");
+    KG_ECK(cudaStreamSynchronize(e->stream));
+    KG_ECK(cudaMemcpy(shells, e->d_feat, sizeof(double) * 4 * e->count, cudaMemcpyDeviceToHost));
+    return KG_OK;
+}
+
+int kg_ens_fetch(int i, double* u) {
+    Ens* e = g_ens;
+    if (!e) return efail(KG_ESTATE, "kg_ens_fetch before kg_ens_init");
+    if (i < 0 || i >= e->count || !u) return efail(KG_EINVAL, "bad instance index or NULL");
+    KG_ECK(cudaStreamSynchronize(e->stream));
+    EnsInst in;
+    KG_ECK(cudaMemcpy(&in, e->d_inst + i, sizeof(EnsInst), cudaMemcpyDeviceToHost));
+    const int N = in.N, NH = N / 2 + 1;
+    const Tables& tb = e->tab[N == 64 ? 0 : 1];
+    const double2* cur = in.phase ? in.S1 : in.S0;
+    KG_ECK(kLaunchF64.col_from_f64(N, cur, cur, nullptr, e->tmp, NH, (size_t)N * NH, N, tb.tw64, e->stream));
+    KG_ECK(kLaunchF64.col(N, +1, e->tmp, (size_t)N * NH, NH, N, tb.tw64, e->stream));
+    KG_ECK(launch_x_inverse(N, e->tmp, e->phys, tb.tw64, 1.0 / ((double)N * N * N), nullptr, e->stream));
+    KG_ECK(cudaMemcpyAsync(u, e->phys, sizeof(double) * (size_t)N * N * N, cudaMemcpyDeviceToHost, e->stream));
+    KG_ECK(cudaStreamSynchronize(e->stream));
+    return KG_OK;
+}
+
+int kg_ens_tune(int steps, int* blocks_per_sm, int* order) {
+    Ens* e = g_ens;
+    if (!e) return efail(KG_ESTATE, "kg_ens_tune before kg_ens_init");
+    if (steps < 1) return efail(KG_EINVAL, "steps < 1");
+    // the candidates advance the ensemble itself: tune on a throw-away ensemble and
+    // initialise the measured one afterwards (the choice is kept for it)
+    const int maxb = e->pl->ens_blocks_per_sm();
+    float best = 1e30f;
+    int bb = 1, bo = 0;
+    for (int o = 0; o < 2; o++) {
+        for (int b = 1; b <= maxb; b++) {
+            int rc = set_shape(e, b, o);
+            if (rc) return rc;
+            rc = launch_steps(e, 1);   // warm-up
+            if (rc) return rc;
+            KG_ECK(cudaEventRecord(e->ev0, e->stream));
+            rc = launch_steps(e, steps);
+            if (rc) return rc;
+            KG_ECK(cudaEventRecord(e->ev1, e->stream));
+            KG_ECK(cudaEventSynchronize(e->ev1));
+            int rs = check_status(e);
+            if (rs) return rs;
+            float t = 0.f;
+            KG_ECK(cudaEventElapsedTime(&t, e->ev0, e->ev1));
+            if (t < best) {
+                best = t;
+                bb = b;
+                bo = o;
+            }
+        }
+    }
+    int rc = set_shape(e, bb, bo);
+    if (rc) return rc;
+    g_tuned.valid = true;
+    g_tuned.prec = e->prec;
+    count_sizes(e->Ns, &g_tuned.n64, &g_tuned.n128);
+    g_tuned.bps = bb;
+    g_tuned.order = bo;
+    if (blocks_per_sm) *blocks_per_sm = bb;
+    if (order) *order = bo;
+    return KG_OK;
+}
+
+int kg_ens_finalize(void) {
+    if (g_ens) {
+        ens_destroy(g_ens);
+        g_ens = nullptr;
+    }
+    return KG_OK;
+}
+
+}  // extern "C"

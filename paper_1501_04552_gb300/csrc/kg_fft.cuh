@@ -241,6 +241,10 @@ struct Stats<PrecF64> {
     }
     __device__ __forceinline__ double total() const { return sum.value(); }
     __device__ __forceinline__ double maxval() const { return __longlong_as_double((long long)mx); }
+    // float bits of max|u| (nan above inf above every finite value)
+    __device__ __forceinline__ unsigned fkey() const {
+        return __float_as_uint(d2f_int(__longlong_as_double((long long)mx))) & 0x7FFFFFFFu;
+    }
 };
 
 template <>
@@ -258,6 +262,7 @@ struct Stats<PrecDF> {
     }
     __device__ __forceinline__ double total() const { return f2d_int(acc.hi) + f2d_int(acc.lo); }
     __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
+    __device__ __forceinline__ unsigned fkey() const { return mx; }
 };
 
 template <>
@@ -275,6 +280,7 @@ struct Stats<PrecF32> {
     }
     __device__ __forceinline__ double total() const { return f2d_int(acc.hi) + f2d_int(acc.lo); }
     __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
+    __device__ __forceinline__ unsigned fkey() const { return mx; }
 };
 
 // ---------------------------------------------------------------------------

@@ -42,33 +42,18 @@ __device__ __forceinline__ void x_load_c2r(const typename P::S* __restrict__ lin
     }
 }
 
+// One x-line (T = N/16 threads, thread j): C2R, scale, stats, and in MODE_STEP the
+// cube, R2C and write-back.  The line is read and written through L.
 template <class P, int N, int MODE>
-__global__ void __launch_bounds__(kXThreads) k_pass_x(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
-                                                      double* __restrict__ part_sum, double* __restrict__ part_max,
-                                                      const typename P::S* __restrict__ tw, double scale, double lam) {
+__device__ __forceinline__ void x_line_body(typename P::S* __restrict__ L, int j, LineSmem<P>& lsm,
+                                            const typename P::S* __restrict__ tw, double scale, typename P::R rlam,
+                                            bool want_sum, Stats<P>& st) {
     typedef typename P::R R;
-    typedef typename P::S S;
     typedef cx<R> C;
-    typedef XShape<N> X;
-    constexpr int M = X::M, T = X::T, NH = N / 2 + 1;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    S* sm = reinterpret_cast<S*>(smraw);
-    __shared__ double red[96];
-
-    const int li = threadIdx.x / T, j = threadIdx.x % T;
-    const size_t line = (size_t)blockIdx.x * X::LPC + li;
-    S* __restrict__ L = W + line * NH;
-    LineSmem<P> lsm{sm + li * X::PADM};
-
-    const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev);
-
+    constexpr int M = N / 2, T = XShape<N>::T;
     C v[8];
     x_load_c2r<P, N>(L, j, tw, v);
     fft<P, M, +1>(v, j, tw, 2, lsm);
-
-    Stats<P> st;
-    st.init();
-    const R rlam = P::from_f64(lam);
 #pragma unroll
     for (int s = 0; s < 8; s++) {
         v[s].re = P::scale2(v[s].re, scale);   // scale = 1/N^3, a power of two
@@ -76,7 +61,6 @@ __global__ void __launch_bounds__(kXThreads) k_pass_x(typename P::S* __restrict_
         st.take(v[s].re, want_sum);
         st.take(v[s].im, want_sum);
     }
-
     if (MODE == MODE_STEP) {
 #pragma unroll
         for (int s = 0; s < 8; s++) {
@@ -104,7 +88,29 @@ __global__ void __launch_bounds__(kXThreads) k_pass_x(typename P::S* __restrict_
             L[k] = P::pack(out);
             if (k == 0) L[M] = P::pack(cmake<R>(Z.re - Z.im, P::from_f64(0.0)));
         }
+        lsm.sync();
     }
+}
+
+template <class P, int N, int MODE>
+__global__ void __launch_bounds__(kXThreads) k_pass_x(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
+                                                      double* __restrict__ part_sum, double* __restrict__ part_max,
+                                                      const typename P::S* __restrict__ tw, double scale, double lam) {
+    typedef typename P::S S;
+    typedef XShape<N> X;
+    constexpr int T = X::T, NH = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    S* sm = reinterpret_cast<S*>(smraw);
+    __shared__ double red[96];
+
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const size_t line = (size_t)blockIdx.x * X::LPC + li;
+    LineSmem<P> lsm{sm + li * X::PADM};
+    const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev);
+
+    Stats<P> st;
+    st.init();
+    x_line_body<P, N, MODE>(W + line * NH, j, lsm, tw, scale, P::from_f64(lam), want_sum, st);
 
     NSum acc;
     acc.s = st.total();
@@ -128,23 +134,15 @@ struct ColShape {
     static constexpr int C = 128 / (int)sizeof(typename P::S);
 };
 
+// one column (T = N/8 threads, thread j) of a tile; valid == false for the columns
+// of the last tile beyond kx = N/2 (they compute on zeros and store nothing)
 template <class Pin, class P, class Pout, int N, int SIGN>
-__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col(const typename Pin::S* src, typename Pout::S* dst,
-                                                               size_t plane_stride, size_t row_stride,
-                                                               const typename P::S* __restrict__ tw) {
+__device__ __forceinline__ void col_body(const typename Pin::S* src, typename Pout::S* dst, size_t base,
+                                         size_t row_stride, bool valid, int j, ColSmem<P, ColShape<P>::C>& csm,
+                                         const typename P::S* __restrict__ tw) {
     typedef typename P::R R;
-    typedef cx<R> Cx;
-    constexpr int C = ColShape<P>::C, T = N / 8, NH = N / 2 + 1;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
-
-    const int c = threadIdx.x % C, j = threadIdx.x / C;
-    const int kx = blockIdx.x * C + c;
-    const bool valid = kx < NH;
-    const size_t base = (size_t)blockIdx.y * plane_stride + kx;
-    ColSmem<P, C> csm{sm, c};
-
-    Cx v[8];
+    constexpr int T = N / 8;
+    cx<R> v[8];
 #pragma unroll
     for (int s = 0; s < 8; s++) {
         if (valid) v[s] = Convert<Pin, P>::go(Pin::load(src[base + (size_t)(j + T * s) * row_stride]));
@@ -157,6 +155,19 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col(const typename P
     }
 }
 
+template <class Pin, class P, class Pout, int N, int SIGN>
+__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col(const typename Pin::S* src, typename Pout::S* dst,
+                                                               size_t plane_stride, size_t row_stride,
+                                                               const typename P::S* __restrict__ tw) {
+    constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const int kx = blockIdx.x * C + c;
+    ColSmem<P, C> csm{sm, c};
+    col_body<Pin, P, Pout, N, SIGN>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NH, j, csm, tw);
+}
+
 // inverse column FFT from an FP64 spectral array into W (precision P); the source is
 // src1 when dev != NULL and dev->phase == 1, src0 otherwise (the current level's array)
 template <class P, int N>
@@ -164,61 +175,33 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col_sel(const double
                                                                    const KgDev* dev, typename P::S* dst,
                                                                    size_t plane_stride, size_t row_stride,
                                                                    const typename P::S* __restrict__ tw) {
-    typedef typename P::R R;
-    typedef cx<R> Cx;
-    constexpr int C = ColShape<P>::C, T = N / 8, NH = N / 2 + 1;
+    constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
-    const double2* __restrict__ src = (dev != nullptr && dev->phase) ? src1 : src0;
-
+    const double2* src = (dev != nullptr && dev->phase) ? src1 : src0;
     const int c = threadIdx.x % C, j = threadIdx.x / C;
     const int kx = blockIdx.x * C + c;
-    const bool valid = kx < NH;
-    const size_t base = (size_t)blockIdx.y * plane_stride + kx;
     ColSmem<P, C> csm{sm, c};
-
-    Cx v[8];
-#pragma unroll
-    for (int s = 0; s < 8; s++) {
-        if (valid) v[s] = Convert<PrecF64, P>::go(PrecF64::load(src[base + (size_t)(j + T * s) * row_stride]));
-        else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
-    }
-    fft<P, N, +1>(v, j, tw, 1, csm);
-    if (valid) {
-#pragma unroll
-        for (int s = 0; s < 8; s++) dst[base + (size_t)(j + T * s) * row_stride] = P::pack(v[s]);
-    }
+    col_body<PrecF64, P, P, N, +1>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NH, j, csm, tw);
 }
 
 // ---------------------------------------------------------------------------
-// Pass Z: forward z FFT -> F^n, FP64 update, optional Q partials, inverse z FFT.
+// Pass Z: forward z FFT -> F^n, FP64 update, optional Q terms, inverse z FFT.
 // coef[m2] = (2 c_k, 2 beta_k) for integer m2 = mx^2 + my^2 + mz^2; w2[m2] = omega_k^2.
 // ---------------------------------------------------------------------------
+// one (ky, kx) column (T = N/8 threads, thread j); update == false leaves the state
+// untouched (a frozen instance); Q terms are added to q when want_q
 template <class P, int N>
-__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_pass_z(typename P::S* __restrict__ W, double2* S0, double2* S1,
-                                                                  KgDev* __restrict__ dev, double* __restrict__ part_sum,
-                                                                  const double2* __restrict__ coef,
-                                                                  const double* __restrict__ w2tab,
-                                                                  const typename P::S* __restrict__ tw, double inv_dt) {
+__device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const double2* __restrict__ cur,
+                                       double2* __restrict__ old, int kx, int ky, bool valid, int j,
+                                       ColSmem<P, ColShape<P>::C>& csm, const typename P::S* __restrict__ tw,
+                                       const double2* __restrict__ coef, const double* __restrict__ w2tab,
+                                       double inv_dt, bool update, bool want_q, NSum& q) {
     typedef typename P::R R;
     typedef cx<R> Cx;
-    constexpr int C = ColShape<P>::C, T = N / 8, NH = N / 2 + 1, NT = C * T;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
-    __shared__ double red[96];
-
-    const int c = threadIdx.x % C, j = threadIdx.x / C;
-    const int kx = blockIdx.x * C + c;
-    const int ky = blockIdx.y;
-    const bool valid = kx < NH;
+    constexpr int T = N / 8, NH = N / 2 + 1;
     const size_t rs = (size_t)N * NH;
     const size_t base = (size_t)ky * NH + kx;
-    ColSmem<P, C> csm{sm, c};
-
-    const bool frozen = dev->frozen != 0;
-    const bool want_q = kg_recording(dev);
-    double2* __restrict__ cur = dev->phase ? S1 : S0;
-    double2* __restrict__ old = dev->phase ? S0 : S1;
 
     Cx v[8];
 #pragma unroll
@@ -231,9 +214,6 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_pass_z(typename P::S
     const int my = ky <= N / 2 ? ky : ky - N;
     const int mxy2 = kx * kx + my * my;
     const double wgt = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
-    NSum q;
-    q.s = 0.0;
-    q.c = 0.0;
 #pragma unroll
     for (int s = 0; s < 8; s++) {
         const int kz = j + T * s;
@@ -246,7 +226,7 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_pass_z(typename P::S
             const double2 b = old[idx];
             double nre = P::fma_into(cf.y, v[s].re, fma(cf.x, a.x, -b.x));
             double nim = P::fma_into(cf.y, v[s].im, fma(cf.x, a.y, -b.y));
-            if (!frozen) old[idx] = make_double2(nre, nim);
+            if (update) old[idx] = make_double2(nre, nim);
             if (want_q) {
                 const double dre = (nre - a.x) * inv_dt, dim = (nim - a.y) * inv_dt;
                 const double sre = nre + a.x, sim = nim + a.y;
@@ -256,16 +236,39 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_pass_z(typename P::S
             v[s] = cmake<R>(P::from_f64(nre), P::from_f64(nim));
         }
     }
-    if (want_q) {
-        double mx = 0.0;
-        block_reduce<NT>(q, mx, red);
-        if (threadIdx.x == 0) part_sum[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = q.value();
-    }
 
     fft<P, N, +1>(v, j, tw, 1, csm);
     if (valid) {
 #pragma unroll
         for (int s = 0; s < 8; s++) W[base + (size_t)(j + T * s) * rs] = P::pack(v[s]);
+    }
+}
+
+template <class P, int N>
+__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_pass_z(typename P::S* __restrict__ W, double2* S0, double2* S1,
+                                                                  KgDev* __restrict__ dev, double* __restrict__ part_sum,
+                                                                  const double2* __restrict__ coef,
+                                                                  const double* __restrict__ w2tab,
+                                                                  const typename P::S* __restrict__ tw, double inv_dt) {
+    constexpr int C = ColShape<P>::C, NH = N / 2 + 1, NT = C * N / 8;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
+    __shared__ double red[96];
+
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const int kx = blockIdx.x * C + c;
+    ColSmem<P, C> csm{sm, c};
+    const bool want_q = kg_recording(dev);
+    double2* cur = dev->phase ? S1 : S0;
+    double2* old = dev->phase ? S0 : S1;
+    NSum q;
+    q.s = 0.0;
+    q.c = 0.0;
+    z_body<P, N>(W, cur, old, kx, blockIdx.y, kx < NH, j, csm, tw, coef, w2tab, inv_dt, dev->frozen == 0, want_q, q);
+    if (want_q) {
+        double mx = 0.0;
+        block_reduce<NT>(q, mx, red);
+        if (threadIdx.x == 0) part_sum[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = q.value();
     }
 }
 

@@ -3,9 +3,13 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <functional>
+#include <string>
+
 namespace kg {
 
 struct KgDev;
+struct EnsParams;
 
 // precision ids match KG_FP64 / KG_DF64 / KG_MIXED of kg.h
 struct PassLaunch {
@@ -21,6 +25,9 @@ struct PassLaunch {
     // z pass with the update; writes z_parts(N) partials when recording
     cudaError_t (*pass_z)(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum, const double2* coef,
                           const double* w2tab, const void* tw, double inv_dt, cudaStream_t st);
+    // one persistent cooperative launch of an ensemble step (kg_ensemble.cuh)
+    cudaError_t (*ens_step)(const EnsParams& p, int grid, cudaStream_t st);
+    int (*ens_blocks_per_sm)();
     int (*x_parts)(int N);
     int (*z_parts)(int N);
     size_t store_bytes;  // bytes of one complex value of W
@@ -44,5 +51,30 @@ cudaError_t launch_fin_peek(const double* ps, const double* pm, int count, KgDev
                             cudaStream_t st);
 cudaError_t launch_fin_z(const double* ps, int count, KgDev* dev, double q_norm, cudaStream_t st);
 cudaError_t launch_fin_sum(const double* ps, int count, double norm, double* out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// shared host helpers (kg_host.cu)
+// ---------------------------------------------------------------------------
+const PassLaunch* launcher_for(int prec);
+
+// device tables of one grid: twiddles exp(-2 pi i j/N) in the pass precision and in
+// FP64, (2 c_k, 2 beta_k) and omega_k^2 by integer m^2 = mx^2 + my^2 + mz^2
+struct Tables {
+    void* tw;
+    double2* tw64;
+    double2* coef;
+    double* w2;
+};
+typedef std::function<int(void**, size_t, const char*)> AllocFn;
+int make_tables(int N, int prec, double L, double dt, const AllocFn& alloc, Tables* t);
+
+// FP64 set-up of one state from the physical field in phys (N^3 doubles, overwritten):
+// S0 = uh^0, S1 = uh^{-1} (startup level), W = yz-inverse of uh^0 in the pass
+// precision; fbuf is an FP64 spectral scratch (may alias W when W holds 16-byte values)
+int init_state(int N, int prec, double dt, double lam, const Tables& tb, double* phys, const double* v0,
+               bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st);
+
+// record a failure for kg_last_error(); returns code
+int set_last_error(int code, const std::string& msg);
 
 }  // namespace kg

@@ -1,5 +1,6 @@
 // kg_launch_impl.cuh -- template launchers, instantiated once per precision.
 #pragma once
+#include "kg_ensemble.cuh"
 #include "kg_kernels.cuh"
 #include "kg_launch.h"
 
@@ -98,6 +99,38 @@ struct Launchers {
     static cudaError_t pass_z(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
                               const double* w2, const void* tw, double inv_dt, cudaStream_t st) {
         KG_DISPATCH_N(N, return pass_z_n<NN>(W, S0, S1, dev, ps, coef, w2, tw, inv_dt, st));
+    }
+    static size_t ens_smem() {
+        typedef EnsUnits<P, 64> U64;
+        typedef EnsUnits<P, 128> U128;
+        size_t a = (size_t)U64::LPU * XShape<64>::PADM, b = (size_t)U128::LPU * XShape<128>::PADM;
+        size_t c = (size_t)U64::TPU * 64 * U64::C, d = (size_t)U128::TPU * 128 * U128::C;
+        size_t m = a > b ? a : b;
+        m = m > c ? m : c;
+        m = m > d ? m : d;
+        return m * sizeof(S);
+    }
+    static int ens_blocks_per_sm() {
+        if (set_smem(k_ens_step<P>, ens_smem()) != cudaSuccess) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<P>, kEnsThreads, ens_smem()) != cudaSuccess)
+            return 0;
+        return n;
+    }
+    static cudaError_t ens_step(const EnsParams& p, int grid, cudaStream_t st) {
+        cudaError_t e = set_smem(k_ens_step<P>, ens_smem());
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kEnsThreads);
+        cfg.dynamicSmemBytes = ens_smem();
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_ens_step<P>, p);
     }
     static int z_parts(int N) {
         const int C = ColShape<P>::C, NH = N / 2 + 1;

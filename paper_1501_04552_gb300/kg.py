@@ -66,6 +66,13 @@ _sig = {
     "kg_memory": ([C.POINTER(C.c_size_t)], C.c_int),
     "kg_last_error": ([], C.c_char_p),
     "kg_energy_q_noalloc": ([C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp], C.c_int),
+    "kg_ens_init": ([C.c_int, _vp, C.c_double, C.c_double, _vp, _vp], C.c_int),
+    "kg_ens_run": ([C.c_int, C.c_double, C.POINTER(C.c_longlong), C.POINTER(C.c_double)], C.c_int),
+    "kg_ens_results": ([_vp, _vp, _vp, _vp], C.c_int),
+    "kg_ens_features": ([_vp], C.c_int),
+    "kg_ens_fetch": ([C.c_int, _vp], C.c_int),
+    "kg_ens_tune": ([C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "kg_ens_finalize": ([], C.c_int),
 }
 _state = {"N": None}
 for _name, (_args, _res) in _sig.items():
@@ -191,4 +198,59 @@ def kg_memory():
 
 def kg_last_error():
     return last_error()
+
+
+# ---------------------------------------------------------------------------
+# batched ensemble
+# ---------------------------------------------------------------------------
+_ens = {"Ns": None}
+
+
+def kg_ens_init(Ns, L, dt, A, s):
+    Ns = np.ascontiguousarray(Ns, dtype=np.int32)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    if not (Ns.size == A.size == s.size):
+        raise ValueError("Ns, A and s must have one entry per instance")
+    _check(lib.kg_ens_init(Ns.size, Ns.ctypes.data, L, dt, A.ctypes.data, s.ctypes.data), "kg_ens_init")
+    _ens["Ns"] = Ns.copy()
+
+
+def kg_ens_run(max_steps, threshold=0.0):
+    done, ms = C.c_longlong(), C.c_double()
+    _check(lib.kg_ens_run(int(max_steps), float(threshold), C.byref(done), C.byref(ms)), "kg_ens_run")
+    return done.value, ms.value
+
+
+def kg_ens_results():
+    n = _ens["Ns"].size
+    fr = np.empty(n, dtype=np.int32)
+    bl = np.empty(n, dtype=np.int64)
+    lv = np.empty(n, dtype=np.int64)
+    mx = np.empty(n, dtype=np.float64)
+    _check(lib.kg_ens_results(fr.ctypes.data, bl.ctypes.data, lv.ctypes.data, mx.ctypes.data), "kg_ens_results")
+    return {"frozen": fr.astype(bool), "blowup_level": bl, "level": lv, "maxabs": mx}
+
+
+def kg_ens_features():
+    out = np.empty((_ens["Ns"].size, 4), dtype=np.float64)
+    _check(lib.kg_ens_features(out.ctypes.data), "kg_ens_features")
+    return out
+
+
+def kg_ens_fetch(i):
+    N = int(_ens["Ns"][i])
+    out = np.empty((N, N, N), dtype=np.float64)
+    _check(lib.kg_ens_fetch(int(i), out.ctypes.data), "kg_ens_fetch")
+    return out
+
+
+def kg_ens_tune(steps=3):
+    b, o = C.c_int(), C.c_int()
+    _check(lib.kg_ens_tune(int(steps), C.byref(b), C.byref(o)), "kg_ens_tune")
+    return b.value, o.value
+
+
+def kg_ens_finalize():
+    _check(lib.kg_ens_finalize(), "kg_ens_finalize")
 
