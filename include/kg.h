@@ -152,6 +152,42 @@ int kg_ens_tune(int steps, int* blocks_per_sm, int* order);
 
 int kg_ens_finalize(void);
 
+/* The same four shell energies for count sampled Gaussians A[i] exp(-|x|^2/s[i]^2) on an
+ * N^3 grid of side L (N even), without building instances (the field is separable, so its
+ * low modes are products of 1D DFT sums).  shells: count x 4 doubles. */
+int kg_gaussian_features(int count, int N, double L, const double* A, const double* s, double* shells);
+
+/* ---- blow-up ranker network ----
+ * The paper motivates parametric blow-up studies (section 1) but has no learned
+ * component; this network is the project's: 6 inputs (A, s and four low-mode shell
+ * energies, normalised by the caller) -> 128 -> 128 -> 2 with ReLU; z0 is the
+ * blow-up logit, z1 the predicted log blow-up time.  Loss (mean over the batch):
+ * BCE(z0, y) + y (z1 - l)^2 + (1 - y) max(log T - z1, 0)^2.  BF16 operands on the
+ * tensor cores with FP32 accumulation; Adam (b1 0.9, b2 0.999, eps 1e-8) on FP32
+ * master weights.  Parameters are one float vector in the order W1 (6 x 128,
+ * row-major [in][out]), b1 (128), W2 (128 x 128), b2, W3 (128 x 2), b3 (2).
+ * All arrays are host memory; X is n x 6 row-major. */
+typedef struct kg_mlp_cfg {
+    int epochs;               /* passes over the data */
+    int batch;                /* rows per Adam step (a trailing partial batch is dropped) */
+    double lr;                /* Adam step size */
+    double T;                 /* censoring time of runs without blow-up */
+    unsigned long long seed;  /* shuffling stream */
+} kg_mlp_cfg;
+
+int kg_mlp_param_count(void);                       /* length of the parameter vector */
+int kg_mlp_set_params(const float* params);         /* also resets Adam's moments and step count */
+int kg_mlp_get_params(float* params);
+/* gradient of the mean loss over the n rows (and the loss) at the current parameters */
+int kg_mlp_grad(const float* X, const float* y, const float* logt, int n, double T, float* grad, double* loss);
+/* one Adam step with a caller-supplied gradient */
+int kg_mlp_adam_step(const float* grad, double lr);
+/* epochs of shuffled mini-batch Adam; *final_loss = mean loss of the last epoch */
+int kg_mlp_train(const float* X, const float* y, const float* logt, int n, const kg_mlp_cfg* cfg, double* final_loss);
+/* p_blowup = sigmoid(z0), logt = z1 (either may be NULL) */
+int kg_mlp_predict(const float* X, int n, float* p_blowup, float* logt);
+int kg_mlp_finalize(void);
+
 /* Quadratic energy Q of a caller-held Fourier state pair, without allocating.
  * The paper has no counterpart: this is a service for callers that cannot call
  * cudaMalloc, such as applications whose device memory belongs to another

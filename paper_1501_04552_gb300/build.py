@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkg.so")
-UNITS = ["kg_inst_df.cu", "kg_inst_f64.cu", "kg_inst_f32.cu", "kg_api.cu", "kg_host.cu", "kg_ensemble.cu", "kg_noalloc.cu"]
+UNITS = ["kg_inst_df.cu", "kg_inst_f64.cu", "kg_inst_f32.cu", "kg_api.cu", "kg_host.cu", "kg_ensemble.cu", "kg_mlp.cu", "kg_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
 

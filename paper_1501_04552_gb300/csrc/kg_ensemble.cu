@@ -85,6 +85,44 @@ __global__ void k_shells(const double2* __restrict__ uh, int N, double L, double
     }
 }
 
+// shell energies of many sampled Gaussians A exp(-|x|^2/s^2) on the N^3 grid: the field
+// is a product g(x) g(y) g(z), so its low modes are A G(mx) G(my) G(mz) with G the 1D DFT
+// of g; one thread per point, same shells and weights as k_shells
+__global__ void k_gauss_shells(int count, int N, double L, const double* __restrict__ A,
+                               const double* __restrict__ S, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double h = L / N, inv_s2 = 1.0 / (S[i] * S[i]);
+    double gr[5] = {0, 0, 0, 0, 0}, gi[5] = {0, 0, 0, 0, 0};   // G(m), m = 0..4 (G(-m) = conj G(m))
+    for (int j = 0; j < N; j++) {
+        const double x = -L / 2 + h * j;
+        const double gv = exp(-x * x * inv_s2);
+        for (int m = 0; m < 5; m++) {
+            double sn, cs;
+            sincospi(-2.0 * (double)((m * j) % N) / (double)N, &sn, &cs);
+            gr[m] += gv * cs;
+            gi[m] += gv * sn;
+        }
+    }
+    double acc[4] = {0, 0, 0, 0};
+    const double kf = 2.0 * 3.14159265358979323846 / L;
+    for (int mz = -4; mz <= 4; mz++)
+        for (int my = -4; my <= 4; my++)
+            for (int mx = 0; mx <= 4; mx++) {
+                const int m2 = mx * mx + my * my + mz * mz;
+                const int sh = (m2 == 0) ? 0 : (m2 <= 1) ? 1 : (m2 <= 4) ? 2 : (m2 <= 16) ? 3 : -1;
+                if (sh < 0) continue;
+                const int ay = my < 0 ? -my : my, az = mz < 0 ? -mz : mz;
+                // |G(mx) G(my) G(mz)|^2 = |G(mx)|^2 |G(|my|)|^2 |G(|mz|)|^2
+                const double p = (gr[mx] * gr[mx] + gi[mx] * gi[mx]) * (gr[ay] * gr[ay] + gi[ay] * gi[ay]) *
+                                 (gr[az] * gr[az] + gi[az] * gi[az]);
+                const double w = (mx == 0) ? 1.0 : 2.0;
+                acc[sh] += w * 0.5 * (1.0 + kf * kf * m2) * A[i] * A[i] * p;
+            }
+    const double norm = h * h * h / ((double)N * N * N);
+    for (int q = 0; q < 4; q++) out[4 * (size_t)i + q] = acc[q] * norm;
+}
+
 struct Ens {
     int count = 0, prec = KG_DF64;
     double L = 0, dt = 0, lam = 1.0;
@@ -478,6 +516,31 @@ int kg_ens_tune(int steps, int* blocks_per_sm, int* order) {
     g_tuned.order = bo;
     if (blocks_per_sm) *blocks_per_sm = bb;
     if (order) *order = bo;
+    return KG_OK;
+}
+
+int kg_gaussian_features(int count, int N, double L, const double* A, const double* s, double* shells) {
+    if (count < 1 || N < 10 || (N & 1) || !(L > 0.0) || !A || !s || !shells) return efail(KG_EINVAL, "bad arguments");
+    double *dA = nullptr, *dS = nullptr, *dO = nullptr;
+    if (cudaMalloc((void**)&dA, sizeof(double) * count) != cudaSuccess ||
+        cudaMalloc((void**)&dS, sizeof(double) * count) != cudaSuccess ||
+        cudaMalloc((void**)&dO, sizeof(double) * 4 * (size_t)count) != cudaSuccess) {
+        cudaFree(dA);
+        cudaFree(dS);
+        cudaGetLastError();
+        return efail(KG_ENOMEM, "feature buffers");
+    }
+    cudaError_t e = cudaMemcpy(dA, A, sizeof(double) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dS, s, sizeof(double) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_gauss_shells<<<(count + 127) / 128, 128>>>(count, N, L, dA, dS, dO);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(shells, dO, sizeof(double) * 4 * (size_t)count, cudaMemcpyDeviceToHost);
+    cudaFree(dA);
+    cudaFree(dS);
+    cudaFree(dO);
+    if (e != cudaSuccess) return efail(KG_ECUDA, std::string("gaussian features: ") + cudaGetErrorString(e));
     return KG_OK;
 }
 

@@ -37,6 +37,11 @@ class kg_options(C.Structure):
                 ("blowup_threshold", C.c_double), ("drift_tol", C.c_double)]
 
 
+class kg_mlp_cfg(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("T", C.c_double),
+                ("seed", C.c_ulonglong)]
+
+
 class KgError(RuntimeError):
     def __init__(self, code, what):
         super().__init__("%s failed with status %d: %s" % (what, code, last_error()))
@@ -73,6 +78,15 @@ _sig = {
     "kg_ens_fetch": ([C.c_int, _vp], C.c_int),
     "kg_ens_tune": ([C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "kg_ens_finalize": ([], C.c_int),
+    "kg_gaussian_features": ([C.c_int, C.c_int, C.c_double, _vp, _vp, _vp], C.c_int),
+    "kg_mlp_param_count": ([], C.c_int),
+    "kg_mlp_set_params": ([_vp], C.c_int),
+    "kg_mlp_get_params": ([_vp], C.c_int),
+    "kg_mlp_grad": ([_vp, _vp, _vp, C.c_int, C.c_double, _vp, C.POINTER(C.c_double)], C.c_int),
+    "kg_mlp_adam_step": ([_vp, C.c_double], C.c_int),
+    "kg_mlp_train": ([_vp, _vp, _vp, C.c_int, C.POINTER(kg_mlp_cfg), C.POINTER(C.c_double)], C.c_int),
+    "kg_mlp_predict": ([_vp, C.c_int, _vp, _vp], C.c_int),
+    "kg_mlp_finalize": ([], C.c_int),
 }
 _state = {"N": None}
 for _name, (_args, _res) in _sig.items():
@@ -253,4 +267,76 @@ def kg_ens_tune(steps=3):
 
 def kg_ens_finalize():
     _check(lib.kg_ens_finalize(), "kg_ens_finalize")
+
+
+def kg_gaussian_features(N, L, A, s):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    out = np.empty((A.size, 4), dtype=np.float64)
+    _check(lib.kg_gaussian_features(A.size, int(N), float(L), A.ctypes.data, s.ctypes.data, out.ctypes.data),
+           "kg_gaussian_features")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# blow-up ranker network
+# ---------------------------------------------------------------------------
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+def kg_mlp_param_count():
+    return lib.kg_mlp_param_count()
+
+
+def kg_mlp_set_params(params):
+    p = _f32(params)
+    if p.size != kg_mlp_param_count():
+        raise ValueError("parameter vector must hold %d values" % kg_mlp_param_count())
+    _check(lib.kg_mlp_set_params(p.ctypes.data), "kg_mlp_set_params")
+
+
+def kg_mlp_get_params():
+    out = np.empty(kg_mlp_param_count(), dtype=np.float32)
+    _check(lib.kg_mlp_get_params(out.ctypes.data), "kg_mlp_get_params")
+    return out
+
+
+def kg_mlp_grad(X, y, logt, T=10.0):
+    X, y, logt = _f32(X), _f32(y), _f32(logt)
+    g = np.empty(kg_mlp_param_count(), dtype=np.float32)
+    loss = C.c_double()
+    _check(lib.kg_mlp_grad(X.ctypes.data, y.ctypes.data, logt.ctypes.data, X.shape[0], T, g.ctypes.data,
+                           C.byref(loss)), "kg_mlp_grad")
+    return loss.value, g
+
+
+def kg_mlp_adam_step(grad, lr=1e-3):
+    g = _f32(grad)
+    _check(lib.kg_mlp_adam_step(g.ctypes.data, lr), "kg_mlp_adam_step")
+
+
+def kg_mlp_train(X, y, logt, epochs=100, batch=256, lr=1e-3, T=10.0, seed=1):
+    X, y, logt = _f32(X), _f32(y), _f32(logt)
+    cfg = kg_mlp_cfg(int(epochs), int(batch), float(lr), float(T), int(seed))
+    loss = C.c_double()
+    _check(lib.kg_mlp_train(X.ctypes.data, y.ctypes.data, logt.ctypes.data, X.shape[0], C.byref(cfg),
+                            C.byref(loss)), "kg_mlp_train")
+    return loss.value
+
+
+def kg_mlp_predict(X):
+    X = _f32(X)
+    n = X.shape[0]
+    p = np.empty(n, dtype=np.float32)
+    t = np.empty(n, dtype=np.float32)
+    _check(lib.kg_mlp_predict(X.ctypes.data, n, p.ctypes.data, t.ctypes.data), "kg_mlp_predict")
+    return p, t
+
+
+def kg_mlp_finalize():
+    _check(lib.kg_mlp_finalize(), "kg_mlp_finalize")
 
