@@ -160,12 +160,17 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-extras", action="store_true", help="skip the other precisions and the cuFFT point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle sample (profiling runs)")
+    ap.add_argument("--ens-steps", type=int, default=200, help="fixed steps of the ensemble comparison")
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid size (512 is the benchmark; smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         args.steps = min(args.steps, 3)
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
+    # energy is recorded on the steps that end at multiples of ENERGY_EVERY; keep the timed
+    # region aligned with that cadence (warm-up and timed steps in whole periods)
+    args.warmup = -(-args.warmup // ENERGY_EVERY) * ENERGY_EVERY
+    args.steps = max(ENERGY_EVERY, -(-args.steps // ENERGY_EVERY) * ENERGY_EVERY)
 
     import torch
     rank, world, local = dist_env()
@@ -203,12 +208,20 @@ def main():
         barrier()
         torch.cuda.synchronize()
         e0.record(stream)
-        kg.kg_step(steps)
+        energies = []
+        left = steps
+        while left > 0:                       # energy every ENERGY_EVERY levels, as the workload asks
+            k = min(ENERGY_EVERY, left)
+            kg.kg_step(k)
+            left -= k
+            if k == ENERGY_EVERY:
+                energies.append(kg.kg_energy(allow_drift=True))
         e1.record(stream)
         e1.synchronize()
         torch.cuda.synchronize()
         barrier()
         ms = e0.elapsed_time(e1)
+        timed_steps.energies = energies
         if world > 1:
             t = torch.tensor([ms], device=f"cuda:{local}")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -219,6 +232,7 @@ def main():
     with ClockSampler(local) as clk:
         ms = timed_steps(prec, args.steps, args.warmup)
     clocks = clk.summary()
+    energies = list(getattr(timed_steps, "energies", []))
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms * 1e-3)
 
@@ -262,10 +276,17 @@ def main():
         for other in ["fp64", "df64", "mixed"]:
             if other == prec:
                 continue
-            steps = max(5, args.steps // (8 if other == "fp64" else 1))
-            o_ms = timed_steps(other, steps, 3)
-            extras[other] = {"steps_per_s": round(steps / (o_ms * 1e-3), 2), "ms_per_step": round(o_ms / steps, 4)}
+            steps = ENERGY_EVERY * max(1, args.steps // (8 if other == "fp64" else 1) // ENERGY_EVERY)
+            o_ms = timed_steps(other, steps, ENERGY_EVERY)
+            o_pass = [t / steps for t in kg.kg_step_timed(steps)]
+            o_bytes, o_step_bytes = algorithmic_bytes(other, NG)
+            extras[other] = {"steps_per_s": round(steps / (o_ms * 1e-3), 2), "ms_per_step": round(o_ms / steps, 4),
+                             "pass_ms": {n: round(t, 4) for n, t in zip(names, o_pass)},
+                             "step_hbm_frac": round(o_step_bytes / (o_ms / steps * 1e-3) / 1e9 / peak, 4)}
         extras["cufft_torch"] = torch_fft_point(u0, local)
+    ens = None
+    if not args.no_extras and rank == 0:
+        ens = ensemble_point(kg, prec, args.ens_steps, torch, stream)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -283,12 +304,55 @@ def main():
                            "precision": prec, "energy_every": ENERGY_EVERY, "parallelism": "replicas",
                            "l2": "inputs larger than L2 (each state array 1.08 GB)"},
                 "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 6 * args.steps + 2 * (args.steps // ENERGY_EVERY) * 0,
-                "other_precisions": extras}
+                "gpu_launches": 6 * args.steps + 2 * (args.steps // ENERGY_EVERY),
+                "energy_series": {"every": ENERGY_EVERY, "first": energies[0] if energies else None,
+                                  "max_rel_drift": (max(abs(e - energies[0]) for e in energies) / abs(energies[0])
+                                                    if energies else None)},
+                "other_precisions": extras, "ensemble": ens}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def ensemble_point(kg, prec, steps, torch, stream):
+    """512 instances (256 x 64^3 + 256 x 128^3, A ~ U[0.5,4], s ~ U[0.5,2], seed 4, dt = 0.005):
+    one persistent launch per step vs the plain one-instance-at-a-time loop (kg_init + kg_step),
+    both for `steps` fixed steps without early exits, same precision"""
+    from paper_1501_04552_gb300 import inputs as I
+    Ns, A, s = I.ensemble_params(512, 4)
+    kg.kg_set_options(precision=prec)
+    kg.kg_ens_init(Ns, L_BOX, DT, A, s)
+    bps, order = kg.kg_ens_tune(2)                 # tuned on a throw-away copy
+    kg.kg_ens_init(Ns, L_BOX, DT, A, s)
+    kg.kg_ens_run(3)
+    done, ms = kg.kg_ens_run(steps, 0.0)
+    res = kg.kg_ens_results()
+    kg.kg_ens_finalize()
+    ens_rate = float(res["level"].sum() - 3 * len(Ns)) / (ms * 1e-3)
+    # plain loop on a sample of the same instances
+    sample = list(range(0, 256, 43)) + list(range(256, 512, 43))
+    plain_steps = max(20, steps // 4)
+    tot_ms, tot_steps = 0.0, 0
+    for i in sample:
+        N = int(Ns[i])
+        kg.kg_init(N, L_BOX, DT, I.gaussian(N, L_BOX, A[i], s[i]), None)
+        kg.kg_step(3)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kg.kg_step(plain_steps)
+        e1.record(stream)
+        e1.synchronize()
+        tot_ms += e0.elapsed_time(e1)
+        tot_steps += plain_steps
+    kg.kg_finalize()
+    plain_rate = tot_steps / (tot_ms * 1e-3)
+    return {"instances": int(len(Ns)), "grids": "256 x 64^3 + 256 x 128^3", "steps": int(done),
+            "instance_steps_per_s": round(ens_rate, 1), "plain_loop_instance_steps_per_s": round(plain_rate, 1),
+            "speedup_vs_plain": round(ens_rate / plain_rate, 3), "precision": prec,
+            "tuned_blocks_per_sm": bps, "tuned_order": order,
+            "plain_sample": "%d instances x %d steps (kg_init + kg_step each)" % (len(sample), plain_steps)}
 
 
 def torch_fft_point(u0, local):

@@ -69,6 +69,8 @@ struct Ctx {
     bool have_E0 = false;
     double E0 = 0.0;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t step_graph = nullptr;   // one captured step, replayed by kg_step
+    long long launched = 0;                 // steps enqueued so far
 };
 
 Ctx* g_ctx = nullptr;
@@ -103,6 +105,7 @@ void destroy(Ctx* c) {
     for (void* p : c->allocs) cudaFree(p);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -272,6 +275,24 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
     return KG_OK;
 }
 
+// capture one step (its six launches) into a graph; every decision of a step is made
+// on the device from KgDev, so the same graph serves every later step
+int ensure_step_graph(Ctx* c, cudaStream_t st) {
+    if (c->step_graph) return KG_OK;
+    cudaGraph_t g = nullptr;
+    KG_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_step(c, st, false, nullptr);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : fail(KG_ECUDA, std::string("step graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&c->step_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(KG_ECUDA, std::string("step graph instantiate: ") + cudaGetErrorString(e));
+    return KG_OK;
+}
+
 int read_dev(Ctx* c, KgDev* d) {
     cudaStream_t st = stream_of(c);
     KG_CK(cudaMemcpyAsync(d, c->dev, sizeof(KgDev), cudaMemcpyDeviceToHost, st));
@@ -320,8 +341,15 @@ int kg_step(int n) {
     if (n < 0) return fail(KG_EINVAL, "n < 0");
     cudaStream_t st = stream_of(c);
     for (int i = 0; i < n; i++) {
-        int rc = launch_step(c, st, false, nullptr);
+        int rc;
+        if (c->launched == 0) {
+            rc = launch_step(c, st, false, nullptr);   // first step direct: it also sets kernel attributes
+        } else {
+            rc = ensure_step_graph(c, st);
+            if (!rc && cudaGraphLaunch(c->step_graph, st) != cudaSuccess) rc = fail(KG_ECUDA, "cudaGraphLaunch(step)");
+        }
         if (rc) return rc;
+        c->launched++;
     }
     return KG_OK;
 }
@@ -335,6 +363,7 @@ int kg_step_timed(int n, float* ms) {
     for (int i = 0; i < n; i++) {
         int rc = launch_step(c, st, true, ms);
         if (rc) return rc;
+        c->launched++;
     }
     return KG_OK;
 }

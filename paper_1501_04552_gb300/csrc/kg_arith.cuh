@@ -58,6 +58,34 @@ __device__ __forceinline__ df operator*(df x, df y) {
     return fast_two_sum(p, e);
 }
 
+// sum without the final renormalisation: hi is the rounded sum of the high parts and lo
+// collects the exact rounding error of that sum plus both low parts.  The pair still
+// represents x + y to within u^2 (|x| + |y|), but |lo| may exceed half an ulp of hi, so a
+// chain of such sums ends with df_norm.
+__device__ __forceinline__ df df_add_lazy(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    return df_make(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ df df_sub_lazy(df x, df y) { return df_add_lazy(x, df_make(-y.hi, -y.lo)); }
+__device__ __forceinline__ df df_norm(df x) { return fast_two_sum(x.hi, x.lo); }
+
+// a.hi b.hi + c.hi d.hi + (low-order terms) with one renormalisation: the two products
+// are split exactly by FMA, their high parts added by two-sum, and every remaining
+// term (product errors, cross terms with the low parts, the two-sum error) summed in
+// float before the final fast two-sum
+__device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
+    const float p1 = __fmul_rn(a.hi, b.hi);
+    const float p2 = __fmul_rn(c.hi, d.hi);
+    const df s = two_sum(p1, p2);
+    float e = __fmaf_rn(a.hi, b.hi, -p1);           // exact error of p1
+    e = __fadd_rn(e, __fmaf_rn(c.hi, d.hi, -p2));   // plus exact error of p2
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    e = __fmaf_rn(c.hi, d.lo, e);
+    e = __fmaf_rn(c.lo, d.hi, e);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, e));
+}
+
 // multiplication by a power of two (exact unless it under/overflows)
 __device__ __forceinline__ df df_scale2(df x, float p2) { return df_make(__fmul_rn(x.hi, p2), __fmul_rn(x.lo, p2)); }
 __device__ __forceinline__ float df_abs_hi(df x) { return fabsf(x.hi); }
@@ -159,6 +187,14 @@ struct PrecF64 {
     static __device__ __forceinline__ R scale2(R x, double p2) { return x * p2; }
     // acc + s * x with x in this precision, everything else FP64
     static __device__ __forceinline__ double fma_into(double s, R x, double acc) { return fma(s, x, acc); }
+    // butterfly arithmetic: sums that may leave the pair unnormalised (double-float only),
+    // the normalisation that ends such a chain, and the twiddle product
+    static __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return a + b; }
+    static __device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return a - b; }
+    static __device__ __forceinline__ R radd(R a, R b) { return a + b; }
+    static __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
+    static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return a; }
+    static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) { return cmul(a, w); }
 };
 
 struct PrecF32 {
@@ -171,6 +207,12 @@ struct PrecF32 {
     static __device__ __forceinline__ R rsqrt2() { return 0.70710678118654752440f; }
     static __device__ __forceinline__ R scale2(R x, double p2) { return x * (float)p2; }
     static __device__ __forceinline__ double fma_into(double s, R x, double acc) { return fma(s, f2d_int(x), acc); }
+    static __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return a + b; }
+    static __device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return a - b; }
+    static __device__ __forceinline__ R radd(R a, R b) { return a + b; }
+    static __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
+    static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return a; }
+    static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) { return cmul(a, w); }
 };
 
 struct PrecDF {
@@ -185,6 +227,19 @@ struct PrecDF {
     static __device__ __forceinline__ R scale2(R x, double p2) { return df_scale2(x, (float)p2); }
     static __device__ __forceinline__ double fma_into(double s, R x, double acc) {
         return fma(s, f2d_int(x.hi), fma(s, f2d_int(x.lo), acc));
+    }
+    static __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) {
+        return cmake<R>(df_add_lazy(a.re, b.re), df_add_lazy(a.im, b.im));
+    }
+    static __device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) {
+        return cmake<R>(df_sub_lazy(a.re, b.re), df_sub_lazy(a.im, b.im));
+    }
+    static __device__ __forceinline__ R radd(R a, R b) { return df_add_lazy(a, b); }
+    static __device__ __forceinline__ R rsub(R a, R b) { return df_sub_lazy(a, b); }
+    static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return cmake<R>(df_norm(a.re), df_norm(a.im)); }
+    // (a.re w.re - a.im w.im, a.re w.im + a.im w.re), one renormalisation per component
+    static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) {
+        return cmake<R>(df_dot2(a.re, w.re, -a.im, w.im), df_dot2(a.re, w.im, a.im, w.re));
     }
 };
 

@@ -52,9 +52,11 @@ __device__ __forceinline__ cx<typename P::R> twiddle(const typename P::S* __rest
 // ---------------------------------------------------------------------------
 // small DFTs, y_k = sum_j u_j exp(SIGN 2 pi i j k / R), in place, natural order
 // ---------------------------------------------------------------------------
+// The sums inside one small DFT use P::cadd / P::csub, which for double-float skip the
+// renormalisation; dft() renormalises the R outputs once at the end.
 template <class P, int SIGN>
 __device__ __forceinline__ void dft2(cx<typename P::R>* u) {
-    cx<typename P::R> a = u[0] + u[1], b = u[0] - u[1];
+    cx<typename P::R> a = P::cadd(u[0], u[1]), b = P::csub(u[0], u[1]);
     u[0] = a;
     u[1] = b;
 }
@@ -62,12 +64,12 @@ __device__ __forceinline__ void dft2(cx<typename P::R>* u) {
 template <class P, int SIGN>
 __device__ __forceinline__ void dft4(cx<typename P::R>* u) {
     typedef cx<typename P::R> C;
-    C t0 = u[0] + u[2], t1 = u[0] - u[2], t2 = u[1] + u[3];
-    C t3 = mul_si<SIGN>(u[1] - u[3]);
-    u[0] = t0 + t2;
-    u[1] = t1 + t3;
-    u[2] = t0 - t2;
-    u[3] = t1 - t3;
+    C t0 = P::cadd(u[0], u[2]), t1 = P::csub(u[0], u[2]), t2 = P::cadd(u[1], u[3]);
+    C t3 = mul_si<SIGN>(P::csub(u[1], u[3]));
+    u[0] = P::cadd(t0, t2);
+    u[1] = P::cadd(t1, t3);
+    u[2] = P::csub(t0, t2);
+    u[3] = P::csub(t1, t3);
 }
 
 template <class P, int SIGN>
@@ -77,20 +79,20 @@ __device__ __forceinline__ void dft8(cx<typename P::R>* u) {
     C a[4], b[4];
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        a[j] = u[j] + u[j + 4];
-        b[j] = u[j] - u[j + 4];
+        a[j] = P::cadd(u[j], u[j + 4]);
+        b[j] = P::csub(u[j], u[j + 4]);
     }
     const R r = P::rsqrt2();
     {   // b1 *= exp(SIGN i pi/4) = (1 + SIGN i)/sqrt2
         C x = b[1];
-        b[1] = SIGN < 0 ? cmake<R>((x.re + x.im) * r, (x.im - x.re) * r)
-                        : cmake<R>((x.re - x.im) * r, (x.im + x.re) * r);
+        b[1] = SIGN < 0 ? cmake<R>(P::radd(x.re, x.im) * r, P::rsub(x.im, x.re) * r)
+                        : cmake<R>(P::rsub(x.re, x.im) * r, P::radd(x.im, x.re) * r);
     }
     b[2] = mul_si<SIGN>(b[2]);
     {   // b3 *= exp(SIGN 3 i pi/4) = (-1 + SIGN i)/sqrt2
         C x = b[3];
-        b[3] = SIGN < 0 ? cmake<R>((x.im - x.re) * r, -(x.im + x.re) * r)
-                        : cmake<R>(-(x.re + x.im) * r, (x.re - x.im) * r);
+        b[3] = SIGN < 0 ? cmake<R>(P::rsub(x.im, x.re) * r, -(P::radd(x.im, x.re) * r))
+                        : cmake<R>(-(P::radd(x.re, x.im) * r), P::rsub(x.re, x.im) * r);
     }
     dft4<P, SIGN>(a);
     dft4<P, SIGN>(b);
@@ -106,6 +108,8 @@ __device__ __forceinline__ void dft(cx<typename P::R>* u) {
     if (RADIX == 8) dft8<P, SIGN>(u);
     else if (RADIX == 4) dft4<P, SIGN>(u);
     else if (RADIX == 2) dft2<P, SIGN>(u);
+#pragma unroll
+    for (int r = 0; r < RADIX; r++) u[r] = P::cnorm(u[r]);
 }
 
 // ---------------------------------------------------------------------------
@@ -157,7 +161,7 @@ __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, cons
         for (int r = 0; r < RADIX; r++) u[r] = v[q + r * Q];
         if (Ns > 1) {
 #pragma unroll
-            for (int r = 1; r < RADIX; r++) u[r] = cmul(u[r], twiddle<P, SIGN>(tw, k * r * (n / (Ns * RADIX)) * twmul));
+            for (int r = 1; r < RADIX; r++) u[r] = P::ctw(u[r], twiddle<P, SIGN>(tw, k * r * (n / (Ns * RADIX)) * twmul));
         }
         dft<P, SIGN, RADIX>(u);
         if (LAST) {
