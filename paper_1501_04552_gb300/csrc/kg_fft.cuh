@@ -27,6 +27,14 @@
 
 namespace kg {
 
+// asynchronous 16-byte global -> shared copy (L2 only), and its completion wait
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // x-pass modes: one stepping pass, or a read-only pass for P^n
 enum { MODE_STEP = 0, MODE_PEEK = 1 };
 
@@ -249,6 +257,8 @@ struct Stats<PrecF64> {
     __device__ __forceinline__ unsigned fkey() const {
         return __float_as_uint(d2f_int(__longlong_as_double((long long)mx))) & 0x7FFFFFFFu;
     }
+    // bits of max|u| as a double: unsigned order = numeric order, nan above inf
+    __device__ __forceinline__ unsigned long long dkey() const { return mx; }
 };
 
 template <>
@@ -267,6 +277,9 @@ struct Stats<PrecDF> {
     __device__ __forceinline__ double total() const { return f2d_int(acc.hi) + f2d_int(acc.lo); }
     __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
     __device__ __forceinline__ unsigned fkey() const { return mx; }
+    __device__ __forceinline__ unsigned long long dkey() const {
+        return (unsigned long long)__double_as_longlong(f2d_int(__uint_as_float(mx)));
+    }
 };
 
 template <>
@@ -285,6 +298,9 @@ struct Stats<PrecF32> {
     __device__ __forceinline__ double total() const { return f2d_int(acc.hi) + f2d_int(acc.lo); }
     __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
     __device__ __forceinline__ unsigned fkey() const { return mx; }
+    __device__ __forceinline__ unsigned long long dkey() const {
+        return (unsigned long long)__double_as_longlong(f2d_int(__uint_as_float(mx)));
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -320,6 +336,27 @@ __device__ __forceinline__ bool kg_recording(const KgDev* dev) {
 __device__ __forceinline__ void nsum_merge(NSum& a, const NSum& b) {
     a.add(b.s);
     a.c += b.c;
+}
+
+// maximum of 64-bit keys over a CTA of NT threads (a power of two) -> thread 0
+template <int NT>
+__device__ __forceinline__ unsigned long long block_max_key(unsigned long long k, unsigned long long* sh) {
+    constexpr unsigned kMask = NT >= 32 ? 0xffffffffu : ((1u << NT) - 1u);
+    constexpr int kOff0 = NT >= 32 ? 16 : NT / 2;
+#pragma unroll
+    for (int o = kOff0; o > 0; o >>= 1) {
+        const unsigned long long b = __shfl_down_sync(kMask, k, o);
+        k = b > k ? b : k;
+    }
+    constexpr int NW = (NT + 31) / 32;
+    if (NW > 1) {
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = k;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 1; w < NW; w++) k = sh[w] > k ? sh[w] : k;
+    }
+    return k;
 }
 
 // NT threads, a power of two; lane 0 of warp 0 ends with the block result

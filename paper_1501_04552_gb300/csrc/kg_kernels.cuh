@@ -35,10 +35,10 @@ __device__ __forceinline__ void x_load_c2r(const typename P::S* __restrict__ lin
             X.im = P::from_f64(0.0);
             Xp.im = P::from_f64(0.0);
         }
-        C A = X + conj(Xp);
-        C B = X - conj(Xp);
+        C A = P::cadd(X, conj(Xp));
+        C B = P::csub(X, conj(Xp));
         C w = twiddle<P, +1>(tw, k);       // exp(+2 pi i k / N)
-        v[s] = A + mul_i(cmul(w, B));
+        v[s] = P::cnorm(P::cadd(A, mul_i(P::ctw(B, w))));
     }
 }
 
@@ -78,11 +78,11 @@ __device__ __forceinline__ void x_line_body(typename P::S* __restrict__ L, int j
             const int k = j + T * s;
             C Z = v[s];
             C Zp = lsm.get((M - k) & (M - 1));
-            C A = Z + conj(Zp);
-            C B = Z - conj(Zp);
+            C A = P::cadd(Z, conj(Zp));
+            C B = P::csub(Z, conj(Zp));
             C w = twiddle<P, -1>(tw, k);   // exp(-2 pi i k / N)
-            C D = mul_i(cmul(w, B));
-            C out = A - D;
+            C D = mul_i(P::ctw(B, w));
+            C out = P::cnorm(P::csub(A, D));
             out.re = P::scale2(out.re, half);
             out.im = P::scale2(out.im, half);
             L[k] = P::pack(out);
@@ -112,14 +112,17 @@ __global__ void __launch_bounds__(kXThreads) k_pass_x(typename P::S* __restrict_
     st.init();
     x_line_body<P, N, MODE>(W + line * NH, j, lsm, tw, scale, P::from_f64(lam), want_sum, st);
 
-    NSum acc;
-    acc.s = st.total();
-    acc.c = 0.0;
-    double mx = st.maxval();
-    block_reduce<kXThreads>(acc, mx, red);
-    if (threadIdx.x == 0) {
-        part_sum[blockIdx.x] = acc.value();
-        part_max[blockIdx.x] = mx;
+    // the max every step (integer keys), the compensated FP64 sum only when it is wanted
+    __shared__ unsigned long long kred[kXThreads / 32];
+    const unsigned long long key = block_max_key<kXThreads>(st.dkey(), kred);
+    if (threadIdx.x == 0) part_max[blockIdx.x] = __longlong_as_double((long long)key);
+    if (want_sum) {
+        NSum acc;
+        acc.s = st.total();
+        acc.c = 0.0;
+        double unused = 0.0;
+        block_reduce<kXThreads>(acc, unused, red);
+        if (threadIdx.x == 0) part_sum[blockIdx.x] = acc.value();
     }
 }
 
@@ -190,18 +193,33 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col_sel(const double
 // coef[m2] = (2 c_k, 2 beta_k) for integer m2 = mx^2 + my^2 + mz^2; w2[m2] = omega_k^2.
 // ---------------------------------------------------------------------------
 // one (ky, kx) column (T = N/8 threads, thread j); update == false leaves the state
-// untouched (a frozen instance); Q terms are added to q when want_q
-template <class P, int N>
+// untouched (a frozen instance); Q terms are added to q when want_q.
+// PF: the state rows this thread updates are prefetched into shared memory by
+// asynchronous copies issued before the forward FFT: 0 none, 1 uh^n only (st_sm holds
+// 8 nt double2, slot s nt + tid), 2 both arrays (16 nt double2, uh^n at (2s) nt + tid,
+// uh^{n-1} at (2s+1) nt + tid); nt = threads of the CTA, tid = this thread's slot.
+template <class P, int N, int PF = 0, int CW = ColShape<P>::C>
 __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const double2* __restrict__ cur,
                                        double2* __restrict__ old, int kx, int ky, bool valid, int j,
-                                       ColSmem<P, ColShape<P>::C>& csm, const typename P::S* __restrict__ tw,
+                                       ColSmem<P, CW>& csm, const typename P::S* __restrict__ tw,
                                        const double2* __restrict__ coef, const double* __restrict__ w2tab,
-                                       double inv_dt, bool update, bool want_q, NSum& q) {
+                                       double inv_dt, bool update, bool want_q, NSum& q, double2* st_sm = nullptr,
+                                       int tid = 0, int nt = 0) {
     typedef typename P::R R;
     typedef cx<R> Cx;
     constexpr int T = N / 8, NH = N / 2 + 1;
     const size_t rs = (size_t)N * NH;
     const size_t base = (size_t)ky * NH + kx;
+
+    if (PF > 0 && valid) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            const size_t idx = base + (size_t)(j + T * s) * rs;
+            cp_async16(st_sm + (size_t)(PF > 1 ? 2 * s : s) * nt + tid, cur + idx);
+            if (PF > 1) cp_async16(st_sm + (size_t)(2 * s + 1) * nt + tid, old + idx);
+        }
+    }
+    if (PF > 0) cp_async_commit();
 
     Cx v[8];
 #pragma unroll
@@ -210,6 +228,7 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
         else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
     }
     fft<P, N, -1>(v, j, tw, 1, csm);
+    if (PF > 0) cp_async_wait_all();   // each thread reads back only its own copies
 
     const int my = ky <= N / 2 ? ky : ky - N;
     const int mxy2 = kx * kx + my * my;
@@ -222,8 +241,8 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
         if (valid) {
             const size_t idx = base + (size_t)kz * rs;
             const double2 cf = __ldg(coef + m2);
-            const double2 a = cur[idx];
-            const double2 b = old[idx];
+            const double2 a = PF > 0 ? st_sm[(size_t)(PF > 1 ? 2 * s : s) * nt + tid] : cur[idx];
+            const double2 b = PF > 1 ? st_sm[(size_t)(2 * s + 1) * nt + tid] : old[idx];
             double nre = P::fma_into(cf.y, v[s].re, fma(cf.x, a.x, -b.x));
             double nim = P::fma_into(cf.y, v[s].im, fma(cf.x, a.y, -b.y));
             if (update) old[idx] = make_double2(nre, nim);
@@ -244,15 +263,26 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
     }
 }
 
+// The stand-alone z pass uses tiles of 64-byte row segments (half the y-pass width) so
+// that two CTAs share an SM and one CTA's FP64 update overlaps another's FFT work; the
+// state rows of a tile are prefetched into shared memory (both arrays for 16-byte W
+// values, uh^n only for FP32 W, whose tiles have twice the threads).
+template <class P>
+struct ZShape {
+    static constexpr int C = 64 / (int)sizeof(typename P::S);
+    static constexpr int PF = sizeof(typename P::S) == 16 ? 2 : 1;
+};
+
 template <class P, int N>
-__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_pass_z(typename P::S* __restrict__ W, double2* S0, double2* S1,
-                                                                  KgDev* __restrict__ dev, double* __restrict__ part_sum,
-                                                                  const double2* __restrict__ coef,
-                                                                  const double* __restrict__ w2tab,
-                                                                  const typename P::S* __restrict__ tw, double inv_dt) {
-    constexpr int C = ColShape<P>::C, NH = N / 2 + 1, NT = C * N / 8;
+__global__ void __launch_bounds__(ZShape<P>::C * N / 8) k_pass_z(typename P::S* __restrict__ W, double2* S0, double2* S1,
+                                                                KgDev* __restrict__ dev, double* __restrict__ part_sum,
+                                                                const double2* __restrict__ coef,
+                                                                const double* __restrict__ w2tab,
+                                                                const typename P::S* __restrict__ tw, double inv_dt) {
+    constexpr int C = ZShape<P>::C, NH = N / 2 + 1, NT = C * N / 8;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
+    double2* st_sm = reinterpret_cast<double2*>(smraw + (size_t)N * C * sizeof(typename P::S));
     __shared__ double red[96];
 
     const int c = threadIdx.x % C, j = threadIdx.x / C;
@@ -264,7 +294,8 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_pass_z(typename P::S
     NSum q;
     q.s = 0.0;
     q.c = 0.0;
-    z_body<P, N>(W, cur, old, kx, blockIdx.y, kx < NH, j, csm, tw, coef, w2tab, inv_dt, dev->frozen == 0, want_q, q);
+    z_body<P, N, ZShape<P>::PF, C>(W, cur, old, kx, blockIdx.y, kx < NH, j, csm, tw, coef, w2tab, inv_dt,
+                                   dev->frozen == 0, want_q, q, st_sm, threadIdx.x, NT);
     if (want_q) {
         double mx = 0.0;
         block_reduce<NT>(q, mx, red);
@@ -280,17 +311,23 @@ constexpr int kFinThreads = 1024;
 __device__ __forceinline__ void fin_reduce(const double* part_sum, const double* part_max, int count, NSum& acc,
                                            double& mx) {
     __shared__ double red[96];
+    __shared__ unsigned long long kred[kFinThreads / 32];
     acc.s = 0.0;
     acc.c = 0.0;
-    mx = 0.0;
+    unsigned long long key = 0ull;
     for (int i = threadIdx.x; i < count; i += kFinThreads) {
-        acc.add(part_sum[i]);
+        if (part_sum) acc.add(part_sum[i]);
         if (part_max) {
-            double m = part_max[i];
-            mx = (m > mx || m != m) ? m : mx;
+            const unsigned long long k = (unsigned long long)__double_as_longlong(part_max[i]);
+            key = k > key ? k : key;
         }
     }
-    block_reduce<kFinThreads>(acc, mx, red);
+    if (part_max) key = block_max_key<kFinThreads>(key, kred);
+    mx = __longlong_as_double((long long)key);
+    if (part_sum) {
+        double unused = 0.0;
+        block_reduce<kFinThreads>(acc, unused, red);
+    }
 }
 
 #ifdef KG_DEFINE_COMMON_KERNELS   // defined by exactly one translation unit
@@ -299,7 +336,7 @@ __global__ void __launch_bounds__(kFinThreads) k_fin_x(const double* part_sum, c
                                                        KgDev* dev, double p_norm) {
     NSum acc;
     double mx;
-    fin_reduce(part_sum, part_max, count, acc, mx);
+    fin_reduce(kg_recording(dev) ? part_sum : nullptr, part_max, count, acc, mx);
     if (threadIdx.x == 0) {
         if (!dev->frozen) {
             dev->maxabs_last = mx;

@@ -6,9 +6,10 @@
 
 namespace kg {
 
+// dynamic shared memory limit of a kernel (static shared memory comes on top, so the
+// attribute is set whatever the size)
 template <class K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -87,8 +88,8 @@ struct Launchers {
     template <int N>
     static cudaError_t pass_z_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
                                 const double* w2, const void* tw, double inv_dt, cudaStream_t st) {
-        constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
-        const size_t smem = (size_t)N * C * sizeof(S);
+        constexpr int C = ZShape<P>::C, NH = N / 2 + 1;
+        const size_t smem = (size_t)N * C * sizeof(S) + (size_t)ZShape<P>::PF * 8 * (C * N / 8) * sizeof(double2);
         auto kern = k_pass_z<P, N>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
@@ -133,7 +134,7 @@ struct Launchers {
         return cudaLaunchKernelEx(&cfg, k_ens_step<P>, p);
     }
     static int z_parts(int N) {
-        const int C = ColShape<P>::C, NH = N / 2 + 1;
+        const int C = ZShape<P>::C, NH = N / 2 + 1;
         return ((NH + C - 1) / C) * N;
     }
 };
