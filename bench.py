@@ -186,6 +186,7 @@ def main():
         torch.distributed.barrier()
     from paper_1501_04552_gb300 import inputs as I
     from paper_1501_04552_gb300 import kg
+    from paper_1501_04552_gb300 import replicas
 
     NG = args.grid
     w = I.bump_noise(NG)
@@ -222,11 +223,7 @@ def main():
         barrier()
         ms = e0.elapsed_time(e1)
         timed_steps.energies = energies
-        if world > 1:
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return replicas.max_over_ranks(ms, device=f"cuda:{local}")
 
     prec = args.precision
     with ClockSampler(local) as clk:
@@ -234,7 +231,7 @@ def main():
     clocks = clk.summary()
     energies = list(getattr(timed_steps, "energies", []))
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms * 1e-3)
+    value = replicas.throughput(args.steps, world, ms * 1e-3)
 
     # per-pass device times (CUDA events on the library's stream) for the roofline
     pass_ms = kg.kg_step_timed(args.steps)
@@ -262,12 +259,8 @@ def main():
     kg.kg_step(args.steps)
     kg.lib.kg_fetch(out.data_ptr())
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * args.steps / t_e2e, "unit": "steps/s",
+    t_e2e = replicas.max_over_ranks(time.perf_counter() - t0, device=f"cuda:{local}")
+    e2e = {"value": replicas.throughput(args.steps, world, t_e2e), "unit": "steps/s",
            "h2d_bytes_per_step": u0.nbytes // args.steps, "d2h_bytes_per_step": out.numel() * 8 // args.steps,
            "what": "kg_init from pinned host u0 + %d steps + kg_fetch to pinned host" % args.steps}
 
@@ -287,6 +280,7 @@ def main():
     ens = None
     if not args.no_extras and rank == 0:
         ens = ensemble_point(kg, prec, args.ens_steps, torch, stream)
+        ens["mixed"] = ensemble_point(kg, "mixed", args.ens_steps, torch, stream)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu:

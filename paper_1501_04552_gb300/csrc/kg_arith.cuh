@@ -195,6 +195,10 @@ struct PrecF64 {
     static __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
     static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return a; }
     static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) { return cmul(a, w); }
+    // x with its sign bit xor-ed with m (m = 0 or 0x80000000): exact negation on demand
+    static __device__ __forceinline__ R flip(R x, unsigned m) {
+        return __hiloint2double(__double2hiint(x) ^ (int)m, __double2loint(x));
+    }
 };
 
 struct PrecF32 {
@@ -213,6 +217,7 @@ struct PrecF32 {
     static __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
     static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return a; }
     static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) { return cmul(a, w); }
+    static __device__ __forceinline__ R flip(R x, unsigned m) { return __uint_as_float(__float_as_uint(x) ^ m); }
 };
 
 struct PrecDF {
@@ -240,6 +245,9 @@ struct PrecDF {
     // (a.re w.re - a.im w.im, a.re w.im + a.im w.re), one renormalisation per component
     static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) {
         return cmake<R>(df_dot2(a.re, w.re, -a.im, w.im), df_dot2(a.re, w.im, a.im, w.re));
+    }
+    static __device__ __forceinline__ R flip(R x, unsigned m) {
+        return df_make(__uint_as_float(__float_as_uint(x.hi) ^ m), __uint_as_float(__float_as_uint(x.lo) ^ m));
     }
 };
 

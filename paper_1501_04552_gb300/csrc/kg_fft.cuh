@@ -50,38 +50,52 @@ struct FftShape {
     static constexpr int T = n / 8;                // threads per line
 };
 
-// twiddle exp(SIGN 2 pi i idx / Ntab) from a table of exp(-2 pi i j / Ntab)
-template <class P, int SIGN>
-__device__ __forceinline__ cx<typename P::R> twiddle(const typename P::S* __restrict__ tw, int idx) {
-    cx<typename P::R> w = P::load(__ldg(tw + idx));
-    return SIGN < 0 ? w : conj(w);
+// The transform sign sg (-1 forward, +1 inverse) is an ordinary argument: where a call
+// passes a literal the compiler folds every sign flip away, and a pass that runs both
+// directions (the x and z passes) keeps one copy of the butterfly code for both.
+__device__ __forceinline__ unsigned sign_mask(int sg) { return sg < 0 ? 0x80000000u : 0u; }
+
+// twiddle exp(sg 2 pi i idx / Ntab) from a table of exp(-2 pi i j / Ntab); the table is
+// in global memory (read through L1) or, in the FP32 column passes, a shared-memory copy
+// (stage_table), so this is a plain load
+template <class P>
+__device__ __forceinline__ cx<typename P::R> twiddle(const typename P::S* __restrict__ tw, int idx, int sg) {
+    cx<typename P::R> w = P::load(tw[idx]);
+    w.im = P::flip(w.im, sign_mask(-sg));   // conjugate for sg = +1
+    return w;
+}
+
+// a * (sg i) = (-sg a.im, sg a.re)
+template <class P>
+__device__ __forceinline__ cx<typename P::R> mul_sgi(cx<typename P::R> a, int sg) {
+    return cmake<typename P::R>(P::flip(a.im, sign_mask(-sg)), P::flip(a.re, sign_mask(sg)));
 }
 
 // ---------------------------------------------------------------------------
-// small DFTs, y_k = sum_j u_j exp(SIGN 2 pi i j k / R), in place, natural order
+// small DFTs, y_k = sum_j u_j exp(sg 2 pi i j k / R), in place, natural order
 // ---------------------------------------------------------------------------
 // The sums inside one small DFT use P::cadd / P::csub, which for double-float skip the
 // renormalisation; dft() renormalises the R outputs once at the end.
-template <class P, int SIGN>
+template <class P>
 __device__ __forceinline__ void dft2(cx<typename P::R>* u) {
     cx<typename P::R> a = P::cadd(u[0], u[1]), b = P::csub(u[0], u[1]);
     u[0] = a;
     u[1] = b;
 }
 
-template <class P, int SIGN>
-__device__ __forceinline__ void dft4(cx<typename P::R>* u) {
+template <class P>
+__device__ __forceinline__ void dft4(cx<typename P::R>* u, int sg) {
     typedef cx<typename P::R> C;
     C t0 = P::cadd(u[0], u[2]), t1 = P::csub(u[0], u[2]), t2 = P::cadd(u[1], u[3]);
-    C t3 = mul_si<SIGN>(P::csub(u[1], u[3]));
+    C t3 = mul_sgi<P>(P::csub(u[1], u[3]), sg);
     u[0] = P::cadd(t0, t2);
     u[1] = P::cadd(t1, t3);
     u[2] = P::csub(t0, t2);
     u[3] = P::csub(t1, t3);
 }
 
-template <class P, int SIGN>
-__device__ __forceinline__ void dft8(cx<typename P::R>* u) {
+template <class P>
+__device__ __forceinline__ void dft8(cx<typename P::R>* u, int sg) {
     typedef typename P::R R;
     typedef cx<R> C;
     C a[4], b[4];
@@ -91,19 +105,18 @@ __device__ __forceinline__ void dft8(cx<typename P::R>* u) {
         b[j] = P::csub(u[j], u[j + 4]);
     }
     const R r = P::rsqrt2();
-    {   // b1 *= exp(SIGN i pi/4) = (1 + SIGN i)/sqrt2
+    const unsigned ms = sign_mask(sg), mns = sign_mask(-sg);
+    {   // b1 *= exp(sg i pi/4) = (1 + sg i)/sqrt2:  (x.re - sg x.im, x.im + sg x.re) / sqrt2
         C x = b[1];
-        b[1] = SIGN < 0 ? cmake<R>(P::radd(x.re, x.im) * r, P::rsub(x.im, x.re) * r)
-                        : cmake<R>(P::rsub(x.re, x.im) * r, P::radd(x.im, x.re) * r);
+        b[1] = cmake<R>(P::radd(x.re, P::flip(x.im, mns)) * r, P::radd(x.im, P::flip(x.re, ms)) * r);
     }
-    b[2] = mul_si<SIGN>(b[2]);
-    {   // b3 *= exp(SIGN 3 i pi/4) = (-1 + SIGN i)/sqrt2
+    b[2] = mul_sgi<P>(b[2], sg);
+    {   // b3 *= exp(sg 3 i pi/4) = (-1 + sg i)/sqrt2:  (-sg x.im - x.re, sg x.re - x.im) / sqrt2
         C x = b[3];
-        b[3] = SIGN < 0 ? cmake<R>(P::rsub(x.im, x.re) * r, -(P::radd(x.im, x.re) * r))
-                        : cmake<R>(-(P::radd(x.re, x.im) * r), P::rsub(x.re, x.im) * r);
+        b[3] = cmake<R>(P::rsub(P::flip(x.im, mns), x.re) * r, P::rsub(P::flip(x.re, ms), x.im) * r);
     }
-    dft4<P, SIGN>(a);
-    dft4<P, SIGN>(b);
+    dft4<P>(a, sg);
+    dft4<P>(b, sg);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         u[2 * k] = a[k];
@@ -111,13 +124,25 @@ __device__ __forceinline__ void dft8(cx<typename P::R>* u) {
     }
 }
 
-template <class P, int SIGN, int RADIX>
-__device__ __forceinline__ void dft(cx<typename P::R>* u) {
-    if (RADIX == 8) dft8<P, SIGN>(u);
-    else if (RADIX == 4) dft4<P, SIGN>(u);
-    else if (RADIX == 2) dft2<P, SIGN>(u);
+template <class P, int RADIX>
+__device__ __forceinline__ void dft(cx<typename P::R>* u, int sg) {
+    if (RADIX == 8) dft8<P>(u, sg);
+    else if (RADIX == 4) dft4<P>(u, sg);
+    else if (RADIX == 2) dft2<P>(u);
 #pragma unroll
     for (int r = 0; r < RADIX; r++) u[r] = P::cnorm(u[r]);
+}
+
+// Copy a twiddle table of n entries into shared memory once per CTA (all threads call
+// it) when the values are 8-byte FP32 pairs: the FP32 column passes are limited by the
+// L1TEX pipe, where the twiddle loads outnumber the data loads.  The 16-byte passes keep
+// the table in L1: their FFT exchanges already fill the shared-memory bandwidth.
+template <class S>
+__device__ __forceinline__ const S* stage_table(const S* __restrict__ g, S* sm, int n) {
+    if (sizeof(S) != 8) return g;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = g[i];
+    __syncthreads();
+    return sm;
 }
 
 // ---------------------------------------------------------------------------
@@ -145,13 +170,13 @@ struct LineSmem {
 
 // ---------------------------------------------------------------------------
 // Stockham stage STAGE of a length-n transform.  Butterfly b (= j + T q) of a
-// radix-R stage with span Ns reads x[b + r n/R], applies exp(SIGN 2 pi i k r/(Ns R))
+// radix-R stage with span Ns reads x[b + r n/R], applies exp(sg 2 pi i k r/(Ns R))
 // (k = b mod Ns), takes the R-point DFT and writes y[(b - k) R + k + r Ns].
 // twmul: table length / n.
 // ---------------------------------------------------------------------------
-template <class P, int n, int SIGN, int STAGE, class SM>
+template <class P, int n, int STAGE, class SM>
 __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw,
-                                          int twmul, SM& sm) {
+                                          int twmul, SM& sm, int sg) {
     typedef cx<typename P::R> C;
     typedef FftShape<n> Sh;
     constexpr int RADIX = (STAGE < Sh::n8) ? 8 : Sh::rem;
@@ -169,9 +194,9 @@ __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, cons
         for (int r = 0; r < RADIX; r++) u[r] = v[q + r * Q];
         if (Ns > 1) {
 #pragma unroll
-            for (int r = 1; r < RADIX; r++) u[r] = P::ctw(u[r], twiddle<P, SIGN>(tw, k * r * (n / (Ns * RADIX)) * twmul));
+            for (int r = 1; r < RADIX; r++) u[r] = P::ctw(u[r], twiddle<P>(tw, k * r * (n / (Ns * RADIX)) * twmul, sg));
         }
-        dft<P, SIGN, RADIX>(u);
+        dft<P, RADIX>(u, sg);
         if (LAST) {
 #pragma unroll
             for (int r = 0; r < RADIX; r++) out[q + r * Q] = u[r];
@@ -192,15 +217,15 @@ __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, cons
     }
 }
 
-// full length-n transform, unnormalised, sign SIGN; in and out: v[s] = x[j + T s]
-template <class P, int n, int SIGN, class SM>
+// full length-n transform, unnormalised, sign sg; in and out: v[s] = x[j + T s]
+template <class P, int n, class SM>
 __device__ __forceinline__ void fft(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw, int twmul,
-                                    SM& sm) {
+                                    SM& sm, int sg) {
     typedef FftShape<n> Sh;
-    fft_stage<P, n, SIGN, 0>(v, j, tw, twmul, sm);
-    if constexpr (Sh::stages > 1) fft_stage<P, n, SIGN, 1>(v, j, tw, twmul, sm);
-    if constexpr (Sh::stages > 2) fft_stage<P, n, SIGN, 2>(v, j, tw, twmul, sm);
-    if constexpr (Sh::stages > 3) fft_stage<P, n, SIGN, 3>(v, j, tw, twmul, sm);
+    fft_stage<P, n, 0>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 1) fft_stage<P, n, 1>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 2) fft_stage<P, n, 2>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 3) fft_stage<P, n, 3>(v, j, tw, twmul, sm, sg);
 }
 
 // ---------------------------------------------------------------------------

@@ -37,7 +37,7 @@ __device__ __forceinline__ void x_load_c2r(const typename P::S* __restrict__ lin
         }
         C A = P::cadd(X, conj(Xp));
         C B = P::csub(X, conj(Xp));
-        C w = twiddle<P, +1>(tw, k);       // exp(+2 pi i k / N)
+        C w = twiddle<P>(tw, k, +1);       // exp(+2 pi i k / N)
         v[s] = P::cnorm(P::cadd(A, mul_i(P::ctw(B, w))));
     }
 }
@@ -53,21 +53,28 @@ __device__ __forceinline__ void x_line_body(typename P::S* __restrict__ L, int j
     constexpr int M = N / 2, T = XShape<N>::T;
     C v[8];
     x_load_c2r<P, N>(L, j, tw, v);
-    fft<P, M, +1>(v, j, tw, 2, lsm);
+    // inverse transform, then (stepping pass) the forward one, through one copy of the code
+#pragma unroll 1
+    for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
+        fft<P, M>(v, j, tw, 2, lsm, dir == 0 ? +1 : -1);
+        if (dir == 0) {
 #pragma unroll
-    for (int s = 0; s < 8; s++) {
-        v[s].re = P::scale2(v[s].re, scale);   // scale = 1/N^3, a power of two
-        v[s].im = P::scale2(v[s].im, scale);
-        st.take(v[s].re, want_sum);
-        st.take(v[s].im, want_sum);
+            for (int s = 0; s < 8; s++) {
+                v[s].re = P::scale2(v[s].re, scale);   // scale = 1/N^3, a power of two
+                v[s].im = P::scale2(v[s].im, scale);
+                st.take(v[s].re, want_sum);
+                st.take(v[s].im, want_sum);
+            }
+            if (MODE == MODE_STEP) {
+#pragma unroll
+                for (int s = 0; s < 8; s++) {
+                    v[s].re = rlam * (v[s].re * v[s].re * v[s].re);
+                    v[s].im = rlam * (v[s].im * v[s].im * v[s].im);
+                }
+            }
+        }
     }
     if (MODE == MODE_STEP) {
-#pragma unroll
-        for (int s = 0; s < 8; s++) {
-            v[s].re = rlam * (v[s].re * v[s].re * v[s].re);
-            v[s].im = rlam * (v[s].im * v[s].im * v[s].im);
-        }
-        fft<P, M, -1>(v, j, tw, 2, lsm);
         // real-to-complex post-processing: X[k] = (Z_k + conj Z_{M-k})/2 - i W^k (Z_k - conj Z_{M-k})/2
 #pragma unroll
         for (int s = 0; s < 8; s++) lsm.put(j + T * s, v[s]);
@@ -80,7 +87,7 @@ __device__ __forceinline__ void x_line_body(typename P::S* __restrict__ L, int j
             C Zp = lsm.get((M - k) & (M - 1));
             C A = P::cadd(Z, conj(Zp));
             C B = P::csub(Z, conj(Zp));
-            C w = twiddle<P, -1>(tw, k);   // exp(-2 pi i k / N)
+            C w = twiddle<P>(tw, k, -1);   // exp(-2 pi i k / N)
             C D = mul_i(P::ctw(B, w));
             C out = P::cnorm(P::csub(A, D));
             out.re = P::scale2(out.re, half);
@@ -151,7 +158,7 @@ __device__ __forceinline__ void col_body(const typename Pin::S* src, typename Po
         if (valid) v[s] = Convert<Pin, P>::go(Pin::load(src[base + (size_t)(j + T * s) * row_stride]));
         else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
     }
-    fft<P, N, SIGN>(v, j, tw, 1, csm);
+    fft<P, N>(v, j, tw, 1, csm, SIGN);
     if (valid) {
 #pragma unroll
         for (int s = 0; s < 8; s++) dst[base + (size_t)(j + T * s) * row_stride] = Pout::pack(Convert<P, Pout>::go(v[s]));
@@ -168,6 +175,7 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col(const typename P
     const int c = threadIdx.x % C, j = threadIdx.x / C;
     const int kx = blockIdx.x * C + c;
     ColSmem<P, C> csm{sm, c};
+    tw = stage_table(tw, sm + N * C, N);
     col_body<Pin, P, Pout, N, SIGN>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NH, j, csm, tw);
 }
 
@@ -185,6 +193,7 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col_sel(const double
     const int c = threadIdx.x % C, j = threadIdx.x / C;
     const int kx = blockIdx.x * C + c;
     ColSmem<P, C> csm{sm, c};
+    tw = stage_table(tw, sm + N * C, N);
     col_body<PrecF64, P, P, N, +1>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NH, j, csm, tw);
 }
 
@@ -227,36 +236,41 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
         if (valid) v[s] = P::load(W[base + (size_t)(j + T * s) * rs]);
         else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
     }
-    fft<P, N, -1>(v, j, tw, 1, csm);
-    if (PF > 0) cp_async_wait_all();   // each thread reads back only its own copies
-
-    const int my = ky <= N / 2 ? ky : ky - N;
-    const int mxy2 = kx * kx + my * my;
-    const double wgt = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
+    // forward z transform, the update, then the inverse z transform; the double-float and
+    // FP64 bodies are large, so they run both transforms through one copy of the FFT code
+    constexpr bool kShare = sizeof(typename P::S) == 16;
+#pragma unroll(kShare ? 1 : 2)
+    for (int dir = 0; dir < 2; dir++) {
+        fft<P, N>(v, j, tw, 1, csm, dir == 0 ? -1 : +1);
+        if (dir == 1) break;
+        if (PF > 0) cp_async_wait_all();   // each thread reads back only its own copies
+        const int my = ky <= N / 2 ? ky : ky - N;
+        const int mxy2 = kx * kx + my * my;
+        const double wgt = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
 #pragma unroll
-    for (int s = 0; s < 8; s++) {
-        const int kz = j + T * s;
-        const int mz = kz <= N / 2 ? kz : kz - N;
-        const int m2 = mxy2 + mz * mz;
-        if (valid) {
-            const size_t idx = base + (size_t)kz * rs;
-            const double2 cf = __ldg(coef + m2);
-            const double2 a = PF > 0 ? st_sm[(size_t)(PF > 1 ? 2 * s : s) * nt + tid] : cur[idx];
-            const double2 b = PF > 1 ? st_sm[(size_t)(2 * s + 1) * nt + tid] : old[idx];
-            double nre = P::fma_into(cf.y, v[s].re, fma(cf.x, a.x, -b.x));
-            double nim = P::fma_into(cf.y, v[s].im, fma(cf.x, a.y, -b.y));
-            if (update) old[idx] = make_double2(nre, nim);
-            if (want_q) {
-                const double dre = (nre - a.x) * inv_dt, dim = (nim - a.y) * inv_dt;
-                const double sre = nre + a.x, sim = nim + a.y;
-                const double term = 0.5 * (dre * dre + dim * dim) + 0.125 * __ldg(w2tab + m2) * (sre * sre + sim * sim);
-                q.add(wgt * term);
+        for (int s = 0; s < 8; s++) {
+            const int kz = j + T * s;
+            const int mz = kz <= N / 2 ? kz : kz - N;
+            const int m2 = mxy2 + mz * mz;
+            if (valid) {
+                const size_t idx = base + (size_t)kz * rs;
+                const double2 cf = __ldg(coef + m2);
+                const double2 a = PF > 0 ? st_sm[(size_t)(PF > 1 ? 2 * s : s) * nt + tid] : cur[idx];
+                const double2 b = PF > 1 ? st_sm[(size_t)(2 * s + 1) * nt + tid] : old[idx];
+                double nre = P::fma_into(cf.y, v[s].re, fma(cf.x, a.x, -b.x));
+                double nim = P::fma_into(cf.y, v[s].im, fma(cf.x, a.y, -b.y));
+                if (update) old[idx] = make_double2(nre, nim);
+                if (want_q) {
+                    const double dre = (nre - a.x) * inv_dt, dim = (nim - a.y) * inv_dt;
+                    const double sre = nre + a.x, sim = nim + a.y;
+                    const double term =
+                        0.5 * (dre * dre + dim * dim) + 0.125 * __ldg(w2tab + m2) * (sre * sre + sim * sim);
+                    q.add(wgt * term);
+                }
+                v[s] = cmake<R>(P::from_f64(nre), P::from_f64(nim));
             }
-            v[s] = cmake<R>(P::from_f64(nre), P::from_f64(nim));
         }
     }
-
-    fft<P, N, +1>(v, j, tw, 1, csm);
     if (valid) {
 #pragma unroll
         for (int s = 0; s < 8; s++) W[base + (size_t)(j + T * s) * rs] = P::pack(v[s]);
@@ -288,6 +302,7 @@ __global__ void __launch_bounds__(ZShape<P>::C * N / 8) k_pass_z(typename P::S* 
     const int c = threadIdx.x % C, j = threadIdx.x / C;
     const int kx = blockIdx.x * C + c;
     ColSmem<P, C> csm{sm, c};
+    tw = stage_table(tw, reinterpret_cast<typename P::S*>(st_sm + (size_t)ZShape<P>::PF * 8 * NT), N);
     const bool want_q = kg_recording(dev);
     double2* cur = dev->phase ? S1 : S0;
     double2* old = dev->phase ? S0 : S1;
@@ -412,7 +427,7 @@ __global__ void __launch_bounds__(kXThreads) k_x_forward(const double* __restric
         }
         v[s] = cmake<double>(a, b);
     }
-    fft<P, M, -1>(v, j, tw, 2, lsm);
+    fft<P, M>(v, j, tw, 2, lsm, -1);
 #pragma unroll
     for (int s = 0; s < 8; s++) lsm.put(j + T * s, v[s]);
     lsm.sync();
@@ -423,7 +438,7 @@ __global__ void __launch_bounds__(kXThreads) k_x_forward(const double* __restric
         C Zp = lsm.get((M - k) & (M - 1));
         C A = Z + conj(Zp);
         C B = Z - conj(Zp);
-        C w = twiddle<P, -1>(tw, k);
+        C w = twiddle<P>(tw, k, -1);
         C D = mul_i(cmul(w, B));
         L[k] = make_double2(0.5 * (A.re - D.re), 0.5 * (A.im - D.im));
         if (k == 0) L[M] = make_double2(Z.re - Z.im, 0.0);
@@ -447,7 +462,7 @@ __global__ void __launch_bounds__(kXThreads) k_x_inverse(const double2* __restri
     LineSmem<P> lsm{sm + li * X::PADM};
     C v[8];
     x_load_c2r<P, N>(in + line * NH, j, tw, v);
-    fft<P, M, +1>(v, j, tw, 2, lsm);
+    fft<P, M>(v, j, tw, 2, lsm, +1);
     NSum acc;
     acc.s = 0.0;
     acc.c = 0.0;

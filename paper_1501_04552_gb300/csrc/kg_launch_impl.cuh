@@ -54,7 +54,7 @@ struct Launchers {
     template <int N, int SIGN>
     static cudaError_t col_n(void* W, size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
         constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
-        const size_t smem = (size_t)N * C * sizeof(S);
+        const size_t smem = (size_t)(N * C + N) * sizeof(S);
         auto kern = k_col<P, P, P, N, SIGN>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
@@ -72,7 +72,7 @@ struct Launchers {
     static cudaError_t col_from_f64_n(const double2* src0, const double2* src1, const KgDev* dev, void* W,
                                       size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
         constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
-        const size_t smem = (size_t)N * C * sizeof(S);
+        const size_t smem = (size_t)(N * C + N) * sizeof(S);
         auto kern = k_col_sel<P, N>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
@@ -89,7 +89,8 @@ struct Launchers {
     static cudaError_t pass_z_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
                                 const double* w2, const void* tw, double inv_dt, cudaStream_t st) {
         constexpr int C = ZShape<P>::C, NH = N / 2 + 1;
-        const size_t smem = (size_t)N * C * sizeof(S) + (size_t)ZShape<P>::PF * 8 * (C * N / 8) * sizeof(double2);
+        const size_t smem =
+            (size_t)(N * C + N) * sizeof(S) + (size_t)ZShape<P>::PF * 8 * (C * N / 8) * sizeof(double2);
         auto kern = k_pass_z<P, N>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
