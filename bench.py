@@ -328,6 +328,7 @@ def ensemble_point(kg, prec, steps, torch, stream):
     sample = list(range(0, 256, 43)) + list(range(256, 512, 43))
     plain_steps = max(20, steps // 4)
     tot_ms, tot_steps = 0.0, 0
+    by_size = {64: [0.0, 0], 128: [0.0, 0]}
     for i in sample:
         N = int(Ns[i])
         kg.kg_init(N, L_BOX, DT, I.gaussian(N, L_BOX, A[i], s[i]), None)
@@ -340,11 +341,17 @@ def ensemble_point(kg, prec, steps, torch, stream):
         e1.synchronize()
         tot_ms += e0.elapsed_time(e1)
         tot_steps += plain_steps
+        by_size[N][0] += e0.elapsed_time(e1)
+        by_size[N][1] += plain_steps
     kg.kg_finalize()
+    # the plain loop's mix is 50/50 in instances like the ensemble, so its rate is the
+    # harmonic combination of the per-size rates
     plain_rate = tot_steps / (tot_ms * 1e-3)
+    plain_by_size = {"%d^3" % n: round(v[1] / (v[0] * 1e-3), 1) for n, v in by_size.items() if v[1]}
     return {"instances": int(len(Ns)), "grids": "256 x 64^3 + 256 x 128^3", "steps": int(done),
             "instance_steps_per_s": round(ens_rate, 1), "plain_loop_instance_steps_per_s": round(plain_rate, 1),
             "speedup_vs_plain": round(ens_rate / plain_rate, 3), "precision": prec,
+            "plain_loop_by_grid": plain_by_size,
             "tuned_blocks_per_sm": bps, "tuned_order": order,
             "plain_sample": "%d instances x %d steps (kg_init + kg_step each)" % (len(sample), plain_steps)}
 

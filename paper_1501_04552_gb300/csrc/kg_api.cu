@@ -190,7 +190,7 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
     KG_TRY(dalloc(c, (void**)&c->S1, sizeof(double2) * c->nspec, "state S1"));
     KG_TRY(dalloc(c, &c->W, c->pl->store_bytes * c->nspec, "work array W"));
     KG_TRY(dalloc(c, (void**)&c->dev, sizeof(KgDev), "device state"));
-    c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->z_parts(N)), kLaunchF64.x_parts(N));
+    c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->update_parts()), kLaunchF64.x_parts(N));
     c->nparts = std::max(c->nparts, 152 * 4);
     KG_TRY(dalloc(c, (void**)&c->part_sum, sizeof(double) * c->nparts, "partials"));
     KG_TRY(dalloc(c, (void**)&c->part_max, sizeof(double) * c->nparts, "partials max"));
@@ -259,8 +259,11 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
     if (timed) KG_CK(cudaEventRecord(c->ev[1], st));
     KG_CK(c->pl->col(N, -1, c->W, (size_t)N * NH, NH, N, c->tw, st));
     if (timed) KG_CK(cudaEventRecord(c->ev[2], st));
-    KG_CK(c->pl->pass_z(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, c->tw, 1.0 / c->dt, st));
-    KG_CK(launch_fin_z(c->part_sum, c->pl->z_parts(N), c->dev, q_norm, st));
+    // z pass: forward z FFT of W -> F^n, the streaming FP64 update, inverse z FFT of uh^{n+1}
+    KG_CK(c->pl->col(N, -1, c->W, NH, (size_t)N * NH, N, c->tw, st));
+    KG_CK(c->pl->update(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, st));
+    KG_CK(c->pl->col(N, +1, c->W, NH, (size_t)N * NH, N, c->tw, st));
+    KG_CK(launch_fin_z(c->part_sum, c->pl->update_parts(), c->dev, q_norm, st));
     if (timed) KG_CK(cudaEventRecord(c->ev[3], st));
     KG_CK(c->pl->col(N, +1, c->W, (size_t)N * NH, NH, N, c->tw, st));
     if (timed) {

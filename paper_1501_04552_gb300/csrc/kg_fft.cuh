@@ -139,10 +139,13 @@ __device__ __forceinline__ void dft(cx<typename P::R>* u, int sg) {
 // the table in L1: their FFT exchanges already fill the shared-memory bandwidth.
 template <class S>
 __device__ __forceinline__ const S* stage_table(const S* __restrict__ g, S* sm, int n) {
-    if (sizeof(S) != 8) return g;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = g[i];
-    __syncthreads();
-    return sm;
+    if constexpr (sizeof(S) != 8) {
+        return g;
+    } else {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = g[i];
+        __syncthreads();
+        return sm;
+    }
 }
 
 // ---------------------------------------------------------------------------

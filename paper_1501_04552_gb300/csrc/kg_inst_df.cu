@@ -4,6 +4,5 @@
 namespace kg {
 template struct Launchers<PrecDF>;
 const PassLaunch kLaunchDF = {
-    &Launchers<PrecDF>::pass_x, &Launchers<PrecDF>::col, &Launchers<PrecDF>::col_from_f64, &Launchers<PrecDF>::pass_z,
-    &Launchers<PrecDF>::ens_step, &Launchers<PrecDF>::ens_blocks_per_sm, &Launchers<PrecDF>::x_parts, &Launchers<PrecDF>::z_parts, sizeof(PrecDF::S)};
+    &Launchers<PrecDF>::pass_x, &Launchers<PrecDF>::col, &Launchers<PrecDF>::col_from_f64, &Launchers<PrecDF>::update, &Launchers<PrecDF>::update_parts, &Launchers<PrecDF>::ens_step, &Launchers<PrecDF>::ens_blocks_per_sm, &Launchers<PrecDF>::x_parts, sizeof(PrecDF::S)};
 }  // namespace kg

@@ -5,8 +5,7 @@
 namespace kg {
 template struct Launchers<PrecF64>;
 const PassLaunch kLaunchF64 = {
-    &Launchers<PrecF64>::pass_x, &Launchers<PrecF64>::col, &Launchers<PrecF64>::col_from_f64, &Launchers<PrecF64>::pass_z,
-    &Launchers<PrecF64>::ens_step, &Launchers<PrecF64>::ens_blocks_per_sm, &Launchers<PrecF64>::x_parts, &Launchers<PrecF64>::z_parts, sizeof(PrecF64::S)};
+    &Launchers<PrecF64>::pass_x, &Launchers<PrecF64>::col, &Launchers<PrecF64>::col_from_f64, &Launchers<PrecF64>::update, &Launchers<PrecF64>::update_parts, &Launchers<PrecF64>::ens_step, &Launchers<PrecF64>::ens_blocks_per_sm, &Launchers<PrecF64>::x_parts, sizeof(PrecF64::S)};
 }  // namespace kg
 
 namespace kg {

@@ -277,44 +277,74 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
     }
 }
 
-// The stand-alone z pass uses tiles of 64-byte row segments (half the y-pass width) so
-// that two CTAs share an SM and one CTA's FP64 update overlaps another's FFT work; the
-// state rows of a tile are prefetched into shared memory (both arrays for 16-byte W
-// values, uh^n only for FP32 W, whose tiles have twice the threads).
-template <class P>
-struct ZShape {
-    static constexpr int C = 64 / (int)sizeof(typename P::S);
-    static constexpr int PF = sizeof(typename P::S) == 16 ? 2 : 1;
-};
+// ---------------------------------------------------------------------------
+// Streaming update (the z pass split in three: forward z FFT, this kernel, inverse z
+// FFT).  W holds F^n_k on entry and uh^{n+1}_k in the pass precision on exit; the state
+// update and the Q terms are those of z_body.  Each thread takes kUpdItems consecutive
+// modes per round and issues all their loads before any arithmetic.
+// ---------------------------------------------------------------------------
+constexpr int kUpdThreads = 256;
+constexpr int kUpdItems = 4;
 
 template <class P, int N>
-__global__ void __launch_bounds__(ZShape<P>::C * N / 8) k_pass_z(typename P::S* __restrict__ W, double2* S0, double2* S1,
-                                                                KgDev* __restrict__ dev, double* __restrict__ part_sum,
-                                                                const double2* __restrict__ coef,
-                                                                const double* __restrict__ w2tab,
-                                                                const typename P::S* __restrict__ tw, double inv_dt) {
-    constexpr int C = ZShape<P>::C, NH = N / 2 + 1, NT = C * N / 8;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
-    double2* st_sm = reinterpret_cast<double2*>(smraw + (size_t)N * C * sizeof(typename P::S));
+__global__ void __launch_bounds__(kUpdThreads) k_update(typename P::S* __restrict__ W, double2* S0, double2* S1,
+                                                       KgDev* __restrict__ dev, double* __restrict__ part_sum,
+                                                       const double2* __restrict__ coef,
+                                                       const double* __restrict__ w2tab, double inv_dt) {
+    typedef typename P::R R;
+    constexpr int NH = N / 2 + 1;
+    constexpr long long kModes = (long long)N * N * NH;
     __shared__ double red[96];
-
-    const int c = threadIdx.x % C, j = threadIdx.x / C;
-    const int kx = blockIdx.x * C + c;
-    ColSmem<P, C> csm{sm, c};
-    tw = stage_table(tw, reinterpret_cast<typename P::S*>(st_sm + (size_t)ZShape<P>::PF * 8 * NT), N);
     const bool want_q = kg_recording(dev);
-    double2* cur = dev->phase ? S1 : S0;
-    double2* old = dev->phase ? S0 : S1;
+    const bool update = dev->frozen == 0;
+    const double2* __restrict__ cur = dev->phase ? S1 : S0;
+    double2* __restrict__ old = dev->phase ? S0 : S1;
     NSum q;
     q.s = 0.0;
     q.c = 0.0;
-    z_body<P, N, ZShape<P>::PF, C>(W, cur, old, kx, blockIdx.y, kx < NH, j, csm, tw, coef, w2tab, inv_dt,
-                                   dev->frozen == 0, want_q, q, st_sm, threadIdx.x, NT);
+    const long long stride = (long long)gridDim.x * kUpdThreads * kUpdItems;
+    for (long long i0 = ((long long)blockIdx.x * kUpdThreads) * kUpdItems + threadIdx.x; i0 < kModes; i0 += stride) {
+        cx<R> f[kUpdItems];
+        double2 a[kUpdItems], b[kUpdItems], cf[kUpdItems];
+        int m2v[kUpdItems];
+        bool ok[kUpdItems];
+#pragma unroll
+        for (int t = 0; t < kUpdItems; t++) {
+            const long long i = i0 + (long long)t * kUpdThreads;
+            ok[t] = i < kModes;
+            const long long ii = ok[t] ? i : 0;
+            const int kx = (int)(ii % NH);
+            const int ky = (int)((ii / NH) % N);
+            const int kz = (int)(ii / ((long long)NH * N));
+            const int my = ky <= N / 2 ? ky : ky - N, mz = kz <= N / 2 ? kz : kz - N;
+            m2v[t] = kx * kx + my * my + mz * mz;
+            f[t] = P::load(W[ii]);
+            a[t] = cur[ii];
+            b[t] = old[ii];
+            cf[t] = __ldg(coef + m2v[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < kUpdItems; t++) {
+            if (!ok[t]) continue;
+            const long long i = i0 + (long long)t * kUpdThreads;
+            const double nre = P::fma_into(cf[t].y, f[t].re, fma(cf[t].x, a[t].x, -b[t].x));
+            const double nim = P::fma_into(cf[t].y, f[t].im, fma(cf[t].x, a[t].y, -b[t].y));
+            if (update) old[i] = make_double2(nre, nim);
+            if (want_q) {
+                const int kx = (int)(i % NH);
+                const double wgt = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
+                const double dre = (nre - a[t].x) * inv_dt, dim = (nim - a[t].y) * inv_dt;
+                const double sre = nre + a[t].x, sim = nim + a[t].y;
+                q.add(wgt * (0.5 * (dre * dre + dim * dim) +
+                             0.125 * __ldg(w2tab + m2v[t]) * (sre * sre + sim * sim)));
+            }
+            W[i] = P::pack(cmake<R>(P::from_f64(nre), P::from_f64(nim)));
+        }
+    }
     if (want_q) {
         double mx = 0.0;
-        block_reduce<NT>(q, mx, red);
-        if (threadIdx.x == 0) part_sum[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = q.value();
+        block_reduce<kUpdThreads>(q, mx, red);
+        if (threadIdx.x == 0) part_sum[blockIdx.x] = q.value();
     }
 }
 

@@ -22,14 +22,15 @@ struct PassLaunch {
     // inverse column FFT from an FP64 spectral source (chosen by dev->phase when src1 != NULL) into W
     cudaError_t (*col_from_f64)(int N, const double2* src0, const double2* src1, const KgDev* dev, void* W,
                                 size_t plane_stride, size_t row_stride, int nplanes, const void* tw, cudaStream_t st);
-    // z pass with the update; writes z_parts(N) partials when recording
-    cudaError_t (*pass_z)(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum, const double2* coef,
-                          const double* w2tab, const void* tw, double inv_dt, cudaStream_t st);
+    // streaming FP64 update between a forward and an inverse z column pass; writes
+    // update_parts() Q partials when recording
+    cudaError_t (*update)(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum, const double2* coef,
+                          const double* w2tab, double inv_dt, cudaStream_t st);
+    int (*update_parts)();
     // one persistent cooperative launch of an ensemble step (kg_ensemble.cuh)
     cudaError_t (*ens_step)(const EnsParams& p, int grid, cudaStream_t st);
     int (*ens_blocks_per_sm)();
     int (*x_parts)(int N);
-    int (*z_parts)(int N);
     size_t store_bytes;  // bytes of one complex value of W
 };
 

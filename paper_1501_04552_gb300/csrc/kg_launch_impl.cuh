@@ -85,22 +85,16 @@ struct Launchers {
         KG_DISPATCH_N(N, return col_from_f64_n<NN>(src0, src1, dev, W, pstride, rstride, nplanes, tw, st));
     }
 
+    static int update_parts() { return 152 * 4; }
     template <int N>
-    static cudaError_t pass_z_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
-                                const double* w2, const void* tw, double inv_dt, cudaStream_t st) {
-        constexpr int C = ZShape<P>::C, NH = N / 2 + 1;
-        const size_t smem =
-            (size_t)(N * C + N) * sizeof(S) + (size_t)ZShape<P>::PF * 8 * (C * N / 8) * sizeof(double2);
-        auto kern = k_pass_z<P, N>;
-        cudaError_t e = set_smem(kern, smem);
-        if (e != cudaSuccess) return e;
-        dim3 grid((NH + C - 1) / C, N);
-        kern<<<grid, C * N / 8, smem, st>>>((S*)W, S0, S1, dev, ps, coef, w2, (const S*)tw, inv_dt);
+    static cudaError_t update_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
+                                const double* w2, double inv_dt, cudaStream_t st) {
+        k_update<P, N><<<update_parts(), kUpdThreads, 0, st>>>((S*)W, S0, S1, dev, ps, coef, w2, inv_dt);
         return cudaGetLastError();
     }
-    static cudaError_t pass_z(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
-                              const double* w2, const void* tw, double inv_dt, cudaStream_t st) {
-        KG_DISPATCH_N(N, return pass_z_n<NN>(W, S0, S1, dev, ps, coef, w2, tw, inv_dt, st));
+    static cudaError_t update(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
+                              const double* w2, double inv_dt, cudaStream_t st) {
+        KG_DISPATCH_N(N, return update_n<NN>(W, S0, S1, dev, ps, coef, w2, inv_dt, st));
     }
     static size_t ens_smem() {
         typedef EnsUnits<P, 64> U64;
@@ -133,10 +127,6 @@ struct Launchers {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         return cudaLaunchKernelEx(&cfg, k_ens_step<P>, p);
-    }
-    static int z_parts(int N) {
-        const int C = ZShape<P>::C, NH = N / 2 + 1;
-        return ((NH + C - 1) / C) * N;
     }
 };
 
