@@ -36,12 +36,13 @@ S_BYTES = N_GRID * N_GRID * (N_GRID // 2 + 1) * 16      # one complex128 half-sp
 
 
 def algorithmic_bytes(prec, n=N_GRID):
-    """bytes an ideal step moves: 4 passes reading and writing W, plus reading uh^n,
-    uh^{n-1} and writing uh^{n+1} (FP64) in the z pass"""
+    """bytes each kernel group of a step must move (W is S or S/2 by precision, the state
+    arrays are S), and the bytes an ideal step moves: four passes reading and writing W
+    plus reading uh^n, uh^{n-1} and writing uh^{n+1} (11 S, or 7 S with FP32 W)"""
     s_bytes = n * n * (n // 2 + 1) * 16
     w = s_bytes if prec in ("fp64", "df64") else s_bytes // 2
-    per_pass = {"x": 2 * w, "yf": 2 * w, "z": 2 * w + 3 * s_bytes, "yi": 2 * w}
-    return per_pass, sum(per_pass.values())
+    per_kernel = {"x": 2 * w, "yf": 2 * w, "zf": 2 * w, "update": 2 * w + 3 * s_bytes, "zi": 2 * w, "yi": 2 * w}
+    return per_kernel, 8 * w + 3 * s_bytes
 
 
 def peaks():
@@ -233,20 +234,25 @@ def main():
     ms_per_step = ms / args.steps
     value = replicas.throughput(args.steps, world, ms * 1e-3)
 
-    # per-pass device times (CUDA events on the library's stream) for the roofline
-    pass_ms = kg.kg_step_timed(args.steps)
-    pass_avg = [t / args.steps for t in pass_ms]
-    per_pass_bytes, step_bytes = algorithmic_bytes(prec, NG)
-    names = ["x", "yf", "z", "yi"]
-    dom = int(np.argmax(pass_avg))
+    # per-kernel device times (CUDA events on the library's stream) for the roofline
+    names = kg.STEP_KERNELS
+    k_avg = [t / args.steps for t in kg.kg_step_timed(args.steps)]
+    k_bytes, step_bytes = algorithmic_bytes(prec, NG)
+    dom = int(np.argmax(k_avg))
     peak, peak_kind = peaks()
-    achieved = per_pass_bytes[names[dom]] / (pass_avg[dom] * 1e-3) / 1e9
+    achieved = k_bytes[names[dom]] / (k_avg[dom] * 1e-3) / 1e9
     step_achieved = step_bytes / (ms_per_step * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "pass_" + names[dom], "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+    per_kernel = {n: {"ms": round(t, 4), "GBps": round(k_bytes[n] / (t * 1e-3) / 1e9, 1),
+                      "frac": round(k_bytes[n] / (t * 1e-3) / 1e9 / peak, 4)} for n, t in zip(names, k_avg)}
+    roofline = {"bound": "hbm", "kernel": "k_pass_x" if names[dom] == "x" else
+                ("k_update" if names[dom] == "update" else "k_col(%s)" % names[dom]),
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "peak_kind": peak_kind,
                 "step_achieved": round(step_achieved, 1), "step_frac": round(step_achieved / peak, 4),
-                "pass_ms": {n: round(t, 4) for n, t in zip(names, pass_avg)},
-                "pass_bytes": per_pass_bytes}
+                "kernels": per_kernel}
+    if prec == "df64":
+        roofline["limiter"] = ("double-float FFT kernels are FP32-issue-bound (x pass: issue active ~72 % in "
+                               "ncu); their HBM fraction is low by construction")
 
     # end to end through the public API with host buffers: pinned u0 -> kg_init, K steps, kg_fetch -> host
     pinned_u0 = torch.from_numpy(u0).pin_memory()
@@ -271,10 +277,10 @@ def main():
                 continue
             steps = ENERGY_EVERY * max(1, args.steps // (8 if other == "fp64" else 1) // ENERGY_EVERY)
             o_ms = timed_steps(other, steps, ENERGY_EVERY)
-            o_pass = [t / steps for t in kg.kg_step_timed(steps)]
+            o_k = [t / steps for t in kg.kg_step_timed(steps)]
             o_bytes, o_step_bytes = algorithmic_bytes(other, NG)
             extras[other] = {"steps_per_s": round(steps / (o_ms * 1e-3), 2), "ms_per_step": round(o_ms / steps, 4),
-                             "pass_ms": {n: round(t, 4) for n, t in zip(names, o_pass)},
+                             "kernel_ms": {n: round(t, 4) for n, t in zip(names, o_k)},
                              "step_hbm_frac": round(o_step_bytes / (o_ms / steps * 1e-3) / 1e9 / peak, 4)}
         extras["cufft_torch"] = torch_fft_point(u0, local)
     ens = None

@@ -108,13 +108,65 @@ int kg_status(long long* level, int* frozen, long long* blowup_level, double* ma
  * interleaved re/im, [kz][ky][kx]) to host memory; either pointer may be NULL. */
 int kg_fetch_spectral(double* a, double* b);
 
-/* Instrumentation: enqueue n steps launching each pass separately, timing each
- * with CUDA events on the context's stream; ms[0..3] receive the summed device
- * time of the x pass, forward y pass, z pass (with the update) and inverse y pass. */
+/* Instrumentation: enqueue n steps launching each kernel separately, timing them
+ * with CUDA events on the context's stream; ms[0..5] receive the summed device time
+ * of the x pass (with its finaliser), forward y, forward z, the update (with its
+ * finaliser), inverse z and inverse y.  Synchronises. */
 int kg_step_timed(int n, float* ms);
 
 /* Bytes of device memory the context holds. */
 int kg_memory(size_t* bytes);
+
+/* ---- checkpoint / resume (the paper has no counterpart; long blow-up runs need it) ----
+ * A checkpoint is one host byte buffer: a kg_state_header followed by the payload,
+ * uh^n then uh^{n-1} (N*N*(N/2+1) complex doubles each, interleaved re/im,
+ * [kz][ky][kx]), in the byte order of the machine that wrote it (little-endian on
+ * both x86-64 and Arm64).  Only the FP64 state is stored: the work array is
+ * rebuilt from uh^n on load by the same inverse transforms a step ends with, so a
+ * resumed run continues bit for bit as the uninterrupted one would. */
+#define KG_STATE_MAGIC "KGSTATE1"
+#define KG_STATE_VERSION 1u
+
+typedef struct kg_state_header {
+    char magic[8];               /* KG_STATE_MAGIC, no terminating NUL */
+    unsigned int version;        /* KG_STATE_VERSION */
+    unsigned int header_bytes;   /* sizeof(kg_state_header) = 256 */
+    int N, precision, energy_every, frozen;
+    double L, dt, nonlinearity, blowup_threshold, drift_tol;
+    long long level;             /* n of uh^n */
+    long long blowup_level;      /* -1 unless frozen */
+    double maxabs_last;          /* max |u| seen by the last step */
+    double P_last;               /* last recorded P and Q with their levels */
+    long long P_last_level;
+    double Q_last;
+    long long Q_last_level;
+    int have_E0, pad0;
+    double E0;                   /* the drift watchdog's first energy */
+    unsigned long long payload_bytes;   /* 2 * 16 * N*N*(N/2+1) */
+    unsigned long long checksum;        /* kg_state_checksum of the payload */
+    unsigned char reserved[256 - 160];  /* zero */
+} kg_state_header;
+
+/* Write the current context into h (cap bytes).  *used receives the checkpoint
+ * size in every case; h == NULL only asks for that size.  Synchronises.
+ * Errors: KG_ESTATE (no context), KG_EINVAL (used NULL, or cap too small: nothing
+ * written), KG_ECUDA. */
+int kg_save_state(void* h, size_t cap, size_t* used);
+
+/* Replace the context by the checkpoint in h (len bytes): the run's grid, time
+ * step and options (precision, energy_every, nonlinearity, blowup_threshold,
+ * drift_tol) become the current ones, as kg_init plus kg_set_options would make
+ * them, and the level, blow-up state and recorded energies are restored.  The
+ * header and the payload checksum are checked before anything is replaced.
+ * Errors: KG_EINVAL (bad magic, version, size, field or checksum) and KG_ENOTSUP
+ * keep the old context and options; after KG_ENOMEM or KG_ECUDA no context remains
+ * and the options are the checkpoint's. */
+int kg_load_state(const void* h, size_t len);
+
+/* 64-bit checksum of a checkpoint payload: the sum, modulo 2^64, of each 8-byte
+ * word rotated left by (its index mod 64), the words read in machine byte order.
+ * n must be a multiple of 8. */
+unsigned long long kg_state_checksum(const void* p, size_t n);
 
 /* ---- batched parametric ensemble (blow-up studies, section 1 of the paper) ----
  * count independent instances (1..1024) on grids Ns[i] in {64, 128}, side L, step dt,

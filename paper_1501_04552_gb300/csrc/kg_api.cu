@@ -15,6 +15,8 @@
 #include <vector>
 
 #include "../../include/kg.h"
+
+static_assert(sizeof(kg_state_header) == 256, "checkpoint header layout");
 #include "kg_fft.cuh"
 #include "kg_launch.h"
 
@@ -68,7 +70,7 @@ struct Ctx {
     size_t bytes = 0;
     bool have_E0 = false;
     double E0 = 0.0;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaGraphExec_t step_graph = nullptr;   // one captured step, replayed by kg_step
     long long launched = 0;                 // steps enqueued so far
 };
@@ -146,18 +148,17 @@ int check_finite(const double* a, size_t n, const char* what) {
     return KG_OK;
 }
 
-int init_common(int N, double L, double dt, const double* u0, const double* v0, bool device_ptrs) {
+int check_grid(int N, double L, double dt) {
     if (!supported_n(N)) return fail(KG_ENOTSUP, "N must be one of 16, 32, 64, 128, 256, 512");
     if (!(L > 0.0) || !std::isfinite(L)) return fail(KG_EINVAL, "L must be finite and > 0");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(KG_EINVAL, "dt must be finite and > 0");
-    if (!u0) return fail(KG_EINVAL, "u0 is NULL");
     if (!launcher(g_opt.precision)) return fail(KG_EINVAL, "unknown precision");
-    const size_t n3 = (size_t)N * N * N;
-    if (!device_ptrs) {
-        int rc = check_finite(u0, n3, "u0");
-        if (!rc && v0) rc = check_finite(v0, n3, "v0");
-        if (rc) return rc;
-    }
+    return KG_OK;
+}
+
+// a context for an N^3 run in the current options, with every buffer a step needs;
+// replaces (destroys) the previous context first.  On failure nothing is kept.
+int create_ctx(int N, double L, double dt, Ctx** out) {
     if (g_ctx) {
         destroy(g_ctx);
         g_ctx = nullptr;
@@ -172,7 +173,7 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
     c->prec = g_opt.precision;
     c->pl = launcher(c->prec);
     c->nspec = (size_t)N * N * c->NH;
-    c->nphys = n3;
+    c->nphys = (size_t)N * N * N;
     int rc = KG_OK;
 #define KG_TRY(x)              \
     do {                       \
@@ -201,7 +202,46 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
         cudaError_t ee = cudaEventCreate(&e);
         if (ee != cudaSuccess) KG_TRY(fail(KG_ECUDA, "cudaEventCreate failed"));
     }
+#undef KG_TRY
+    *out = c;
+    return KG_OK;
+}
 
+KgDev fresh_dev() {
+    KgDev d;
+    std::memset(&d, 0, sizeof(d));
+    d.level = 0;
+    d.phase = 0;
+    d.frozen = 0;
+    d.blowup_level = -1;
+    d.energy_every = g_opt.energy_every;
+    d.threshold = g_opt.blowup_threshold;
+    d.P_last_level = -1000;
+    d.Q_last_level = -1000;
+    return d;
+}
+
+int init_common(int N, double L, double dt, const double* u0, const double* v0, bool device_ptrs) {
+    int rc = check_grid(N, L, dt);
+    if (rc) return rc;
+    if (!u0) return fail(KG_EINVAL, "u0 is NULL");
+    const size_t n3 = (size_t)N * N * N;
+    if (!device_ptrs) {
+        rc = check_finite(u0, n3, "u0");
+        if (!rc && v0) rc = check_finite(v0, n3, "v0");
+        if (rc) return rc;
+    }
+    Ctx* c = nullptr;
+    rc = create_ctx(N, L, dt, &c);
+    if (rc) return rc;
+#define KG_TRY(x)              \
+    do {                       \
+        rc = (x);              \
+        if (rc) {              \
+            destroy(c);        \
+            return rc;         \
+        }                      \
+    } while (0)
     cudaStream_t st = stream_of(c);
     // F^0 = R2C(lam u0^3) goes to W viewed as FP64 when it is large enough, else to a set-up scratch
     double2* fbuf = nullptr;
@@ -219,16 +259,7 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
     }
     Tables tb{c->tw, c->tw64, c->coef, c->w2};
     KG_TRY(init_state(N, c->prec, dt, c->lam, tb, c->phys, v0, device_ptrs, c->S0, c->S1, c->W, fbuf, st));
-    KgDev d;
-    std::memset(&d, 0, sizeof(d));
-    d.level = 0;
-    d.phase = 0;
-    d.frozen = 0;
-    d.blowup_level = -1;
-    d.energy_every = g_opt.energy_every;
-    d.threshold = g_opt.blowup_threshold;
-    d.P_last_level = -1000;
-    d.Q_last_level = -1000;
+    KgDev d = fresh_dev();
     if (cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "dev upload"));
     {
         cudaError_t e = cudaStreamSynchronize(st);
@@ -248,28 +279,33 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
     return KG_OK;
 }
 
+// one step; with timed, CUDA events split it into six kernel groups and ms[0..5]
+// accumulate their device times: x pass (+ its finaliser), forward y, forward z, update
+// (+ its finaliser), inverse z, inverse y
 int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
     const int N = c->N, NH = c->NH;
     const double h = c->L / N;
     const double p_norm = c->lam * h * h * h / 4.0;
     const double q_norm = h * h * h * inv_n3(N);
+    const size_t yps = (size_t)N * NH, zrs = (size_t)N * NH;
     if (timed) KG_CK(cudaEventRecord(c->ev[0], st));
     KG_CK(c->pl->pass_x(N, MODE_STEP, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
     KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->x_parts(N), c->dev, p_norm, st));
     if (timed) KG_CK(cudaEventRecord(c->ev[1], st));
-    KG_CK(c->pl->col(N, -1, c->W, (size_t)N * NH, NH, N, c->tw, st));
+    KG_CK(c->pl->col(N, -1, c->W, yps, NH, N, c->tw, st));                        // forward y
     if (timed) KG_CK(cudaEventRecord(c->ev[2], st));
-    // z pass: forward z FFT of W -> F^n, the streaming FP64 update, inverse z FFT of uh^{n+1}
-    KG_CK(c->pl->col(N, -1, c->W, NH, (size_t)N * NH, N, c->tw, st));
-    KG_CK(c->pl->update(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, st));
-    KG_CK(c->pl->col(N, +1, c->W, NH, (size_t)N * NH, N, c->tw, st));
-    KG_CK(launch_fin_z(c->part_sum, c->pl->update_parts(), c->dev, q_norm, st));
+    KG_CK(c->pl->col(N, -1, c->W, NH, zrs, N, c->tw, st));                        // forward z -> F^n
     if (timed) KG_CK(cudaEventRecord(c->ev[3], st));
-    KG_CK(c->pl->col(N, +1, c->W, (size_t)N * NH, NH, N, c->tw, st));
+    KG_CK(c->pl->update(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, st));
+    KG_CK(launch_fin_z(c->part_sum, c->pl->update_parts(), c->dev, q_norm, st));
+    if (timed) KG_CK(cudaEventRecord(c->ev[4], st));
+    KG_CK(c->pl->col(N, +1, c->W, NH, zrs, N, c->tw, st));                        // inverse z
+    if (timed) KG_CK(cudaEventRecord(c->ev[5], st));
+    KG_CK(c->pl->col(N, +1, c->W, yps, NH, N, c->tw, st));                        // inverse y
     if (timed) {
-        KG_CK(cudaEventRecord(c->ev[4], st));
-        KG_CK(cudaEventSynchronize(c->ev[4]));
-        for (int p = 0; p < 4; p++) {
+        KG_CK(cudaEventRecord(c->ev[6], st));
+        KG_CK(cudaEventSynchronize(c->ev[6]));
+        for (int p = 0; p < 6; p++) {
             float t = 0.f;
             KG_CK(cudaEventElapsedTime(&t, c->ev[p], c->ev[p + 1]));
             ms[p] += t;
@@ -361,7 +397,7 @@ int kg_step_timed(int n, float* ms) {
     Ctx* c = g_ctx;
     if (!c) return fail(KG_ESTATE, "kg_step_timed before kg_init");
     if (n < 0 || !ms) return fail(KG_EINVAL, "bad arguments");
-    for (int p = 0; p < 4; p++) ms[p] = 0.f;
+    for (int p = 0; p < 6; p++) ms[p] = 0.f;
     cudaStream_t st = stream_of(c);
     for (int i = 0; i < n; i++) {
         int rc = launch_step(c, st, true, ms);
@@ -521,6 +557,125 @@ int kg_get_options(kg_options* o) {
 int kg_memory(size_t* bytes) {
     if (!bytes) return fail(KG_EINVAL, "NULL");
     *bytes = g_ctx ? g_ctx->bytes : 0;
+    return KG_OK;
+}
+
+unsigned long long kg_state_checksum(const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    unsigned long long sum = 0;
+    for (size_t i = 0; i < n / 8; i++) {
+        unsigned long long w;
+        std::memcpy(&w, b + 8 * i, 8);
+        const unsigned r = (unsigned)(i & 63);
+        sum += r ? (w << r) | (w >> (64 - r)) : w;
+    }
+    return sum;
+}
+
+int kg_save_state(void* h, size_t cap, size_t* used) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_save_state before kg_init");
+    if (!used) return fail(KG_EINVAL, "used is NULL");
+    const size_t arr = sizeof(double2) * c->nspec;
+    const size_t need = sizeof(kg_state_header) + 2 * arr;
+    *used = need;
+    if (!h) return KG_OK;
+    if (cap < need) return fail(KG_EINVAL, "checkpoint buffer smaller than kg_save_state(NULL) reported");
+    KgDev d;
+    int rc = read_dev(c, &d);
+    if (rc) return rc;
+    kg_state_header hd;
+    std::memset(&hd, 0, sizeof(hd));
+    std::memcpy(hd.magic, KG_STATE_MAGIC, 8);
+    hd.version = KG_STATE_VERSION;
+    hd.header_bytes = (unsigned)sizeof(hd);
+    hd.N = c->N;
+    hd.precision = c->prec;
+    hd.energy_every = d.energy_every;
+    hd.frozen = d.frozen;
+    hd.L = c->L;
+    hd.dt = c->dt;
+    hd.nonlinearity = c->lam;
+    hd.blowup_threshold = d.threshold;
+    hd.drift_tol = g_opt.drift_tol;
+    hd.level = d.level;
+    hd.blowup_level = d.blowup_level;
+    hd.maxabs_last = d.maxabs_last;
+    hd.P_last = d.P_last;
+    hd.P_last_level = d.P_last_level;
+    hd.Q_last = d.Q_last;
+    hd.Q_last_level = d.Q_last_level;
+    hd.have_E0 = c->have_E0 ? 1 : 0;
+    hd.E0 = c->E0;
+    hd.payload_bytes = 2 * arr;
+    unsigned char* base = (unsigned char*)h;
+    cudaStream_t st = stream_of(c);
+    const double2* cur = d.phase ? c->S1 : c->S0;
+    const double2* old = d.phase ? c->S0 : c->S1;
+    KG_CK(cudaMemcpyAsync(base + sizeof(hd), cur, arr, cudaMemcpyDeviceToHost, st));
+    KG_CK(cudaMemcpyAsync(base + sizeof(hd) + arr, old, arr, cudaMemcpyDeviceToHost, st));
+    KG_CK(cudaStreamSynchronize(st));
+    hd.checksum = kg_state_checksum(base + sizeof(hd), 2 * arr);
+    std::memcpy(base, &hd, sizeof(hd));
+    return KG_OK;
+}
+
+int kg_load_state(const void* h, size_t len) {
+    if (!h) return fail(KG_EINVAL, "checkpoint pointer is NULL");
+    if (len < sizeof(kg_state_header)) return fail(KG_EINVAL, "checkpoint shorter than its header");
+    kg_state_header hd;
+    std::memcpy(&hd, h, sizeof(hd));
+    if (std::memcmp(hd.magic, KG_STATE_MAGIC, 8) != 0) return fail(KG_EINVAL, "not a checkpoint (magic)");
+    if (hd.version != KG_STATE_VERSION) return fail(KG_EINVAL, "unknown checkpoint version");
+    if (hd.header_bytes != sizeof(hd)) return fail(KG_EINVAL, "checkpoint header size mismatch");
+    if (!supported_n(hd.N)) return fail(KG_ENOTSUP, "checkpoint N not supported");
+    if (!launcher(hd.precision)) return fail(KG_EINVAL, "checkpoint precision unknown");
+    if (!(hd.L > 0.0) || !std::isfinite(hd.L) || !(hd.dt > 0.0) || !std::isfinite(hd.dt) ||
+        !std::isfinite(hd.nonlinearity) || !std::isfinite(hd.blowup_threshold) || !std::isfinite(hd.drift_tol) ||
+        hd.energy_every < 0 || hd.level < 0 || (hd.frozen != 0 && hd.frozen != 1))
+        return fail(KG_EINVAL, "checkpoint header field out of range");
+    const size_t nspec = (size_t)hd.N * hd.N * (hd.N / 2 + 1);
+    const size_t arr = sizeof(double2) * nspec;
+    if (hd.payload_bytes != 2 * arr) return fail(KG_EINVAL, "checkpoint payload size does not match N");
+    if (len < sizeof(hd) + 2 * arr) return fail(KG_EINVAL, "checkpoint truncated");
+    const unsigned char* base = (const unsigned char*)h;
+    if (kg_state_checksum(base + sizeof(hd), 2 * arr) != hd.checksum) return fail(KG_EINVAL, "checkpoint checksum mismatch");
+
+    kg_options o = g_opt;
+    o.precision = hd.precision;
+    o.energy_every = hd.energy_every;
+    o.nonlinearity = hd.nonlinearity;
+    o.blowup_threshold = hd.blowup_threshold;
+    o.drift_tol = hd.drift_tol;
+    g_opt = o;
+    Ctx* c = nullptr;
+    int rc = create_ctx(hd.N, hd.L, hd.dt, &c);
+    if (rc) return rc;
+    const int N = c->N, NH = c->NH;
+    cudaStream_t st = stream_of(c);
+    KgDev d = fresh_dev();
+    d.level = hd.level;
+    d.frozen = hd.frozen;
+    d.blowup_level = hd.blowup_level;
+    d.maxabs_last = hd.maxabs_last;
+    d.P_last = hd.P_last;
+    d.P_last_level = hd.P_last_level;
+    d.Q_last = hd.Q_last;
+    d.Q_last_level = hd.Q_last_level;
+    cudaError_t e = cudaMemcpyAsync(c->S0, base + sizeof(hd), arr, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->S1, base + sizeof(hd) + arr, arr, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st);
+    // W = the yz inverse of uh^n in the pass precision, as the last two transforms of a step leave it
+    if (e == cudaSuccess) e = c->pl->col_from_f64(N, c->S0, c->S1, nullptr, c->W, NH, (size_t)N * NH, N, c->tw, st);
+    if (e == cudaSuccess) e = c->pl->col(N, +1, c->W, (size_t)N * NH, NH, N, c->tw, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        destroy(c);
+        return fail(KG_ECUDA, std::string("kg_load_state: ") + cudaGetErrorString(e));
+    }
+    c->have_E0 = hd.have_E0 != 0;
+    c->E0 = hd.E0;
+    g_ctx = c;
     return KG_OK;
 }
 

@@ -69,6 +69,9 @@ _sig = {
     "kg_fetch_spectral": ([_vp, _vp], C.c_int),
     "kg_step_timed": ([C.c_int, C.POINTER(C.c_float)], C.c_int),
     "kg_memory": ([C.POINTER(C.c_size_t)], C.c_int),
+    "kg_save_state": ([_vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
+    "kg_load_state": ([_vp, C.c_size_t], C.c_int),
+    "kg_state_checksum": ([_vp, C.c_size_t], C.c_ulonglong),
     "kg_last_error": ([], C.c_char_p),
     "kg_energy_q_noalloc": ([C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp], C.c_int),
     "kg_ens_init": ([C.c_int, _vp, C.c_double, C.c_double, _vp, _vp], C.c_int),
@@ -198,16 +201,65 @@ def kg_fetch_spectral(N):
     return a, b
 
 
+STEP_KERNELS = ["x", "yf", "zf", "update", "zi", "yi"]
+
+
 def kg_step_timed(n):
-    ms = (C.c_float * 4)()
+    """summed device ms of the six kernel groups of a step (names in STEP_KERNELS)"""
+    ms = (C.c_float * 6)()
     _check(lib.kg_step_timed(int(n), ms), "kg_step_timed")
-    return [ms[i] for i in range(4)]
+    return [ms[i] for i in range(6)]
 
 
 def kg_memory():
     b = C.c_size_t()
     _check(lib.kg_memory(C.byref(b)), "kg_memory")
     return b.value
+
+
+class kg_state_header(C.Structure):
+    """mirror of kg_state_header in include/kg.h (256 bytes, machine byte order)"""
+    _fields_ = [("magic", C.c_char * 8), ("version", C.c_uint), ("header_bytes", C.c_uint),
+                ("N", C.c_int), ("precision", C.c_int), ("energy_every", C.c_int), ("frozen", C.c_int),
+                ("L", C.c_double), ("dt", C.c_double), ("nonlinearity", C.c_double),
+                ("blowup_threshold", C.c_double), ("drift_tol", C.c_double),
+                ("level", C.c_longlong), ("blowup_level", C.c_longlong), ("maxabs_last", C.c_double),
+                ("P_last", C.c_double), ("P_last_level", C.c_longlong), ("Q_last", C.c_double),
+                ("Q_last_level", C.c_longlong), ("have_E0", C.c_int), ("pad0", C.c_int), ("E0", C.c_double),
+                ("payload_bytes", C.c_ulonglong), ("checksum", C.c_ulonglong), ("reserved", C.c_ubyte * 96)]
+
+
+STATE_HEADER_BYTES = 256
+KG_STATE_MAGIC = b"KGSTATE1"
+KG_STATE_VERSION = 1
+
+
+def state_header(buf):
+    """the kg_state_header at the start of a checkpoint buffer"""
+    return kg_state_header.from_buffer_copy(np.ascontiguousarray(buf[:STATE_HEADER_BYTES]).tobytes())
+
+
+def kg_save_state():
+    """the context as one checkpoint buffer (numpy uint8: 256-byte header, then the state)"""
+    need = C.c_size_t(0)
+    _check(lib.kg_save_state(None, 0, C.byref(need)), "kg_save_state")
+    buf = np.empty(need.value, dtype=np.uint8)
+    _check(lib.kg_save_state(buf.ctypes.data, buf.size, C.byref(need)), "kg_save_state")
+    return buf
+
+
+def kg_load_state(buf):
+    """replace the context by a checkpoint written by kg_save_state"""
+    b = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if not isinstance(buf, np.ndarray) else buf)
+    if b.dtype != np.uint8:
+        b = b.view(np.uint8)
+    _check(lib.kg_load_state(b.ctypes.data, b.size), "kg_load_state")
+    _state["N"] = state_header(b).N
+
+
+def kg_state_checksum(payload):
+    b = np.ascontiguousarray(payload).view(np.uint8)
+    return int(lib.kg_state_checksum(b.ctypes.data, b.size))
 
 
 def kg_last_error():

@@ -60,3 +60,80 @@ def test_options_round_trip_and_validation(kg):
     assert kg.lib.kg_set_options(C.byref(bad)) == kg.KG_EINVAL
     kg.kg_set_options()
     assert kg.kg_get_options()["precision"] == kg.KG_DF64
+
+
+def _rotl_sum(payload):
+    """the checkpoint checksum as kg.h defines it: sum mod 2^64 of word i rotated left by i mod 64"""
+    w = np.frombuffer(payload.tobytes(), dtype="<u8")
+    r = (np.arange(w.size) % 64).astype(np.uint64)
+    rot = np.where(r == 0, w, (w << r) | (w >> ((np.uint64(64) - r) % np.uint64(64))))
+    return int(sum(int(x) for x in rot) % (1 << 64))
+
+
+def test_state_checksum_definition(kg):
+    rng = np.random.default_rng(9)
+    for n in (0, 8, 8 * 63, 8 * 64, 8 * 65, 8 * 1000):
+        p = rng.integers(0, 256, size=n, dtype=np.uint8)
+        assert kg.kg_state_checksum(p) == _rotl_sum(p)
+    # order matters: swapping two distinct words changes the sum
+    p = np.arange(16, dtype=np.uint64).view(np.uint8)
+    q = p.copy().view(np.uint64)
+    q[[2, 3]] = q[[3, 2]]
+    assert kg.kg_state_checksum(p) != kg.kg_state_checksum(q.view(np.uint8))
+
+
+def _checkpoint(kg, N=16, **over):
+    h = kg.kg_state_header()
+    h.magic = kg.KG_STATE_MAGIC
+    h.version = kg.KG_STATE_VERSION
+    h.header_bytes = kg.STATE_HEADER_BYTES
+    h.N, h.precision, h.energy_every, h.frozen = N, kg.KG_DF64, 0, 0
+    h.L, h.dt, h.nonlinearity = 32.0, 0.01, 1.0
+    h.blowup_level = -1
+    arr = 16 * N * N * (N // 2 + 1)
+    payload = np.random.default_rng(1).integers(0, 256, size=2 * arr, dtype=np.uint8)
+    h.payload_bytes = 2 * arr
+    h.checksum = kg.kg_state_checksum(payload)
+    for k, v in over.items():
+        setattr(h, k, v)
+    return np.concatenate([np.frombuffer(bytes(h), dtype=np.uint8), payload])
+
+
+def test_checkpoint_rejected_on_the_host(kg):
+    """every malformed checkpoint is refused before any CUDA call, with KG_EINVAL or KG_ENOTSUP"""
+    kg.lib.kg_finalize()
+    used = C.c_size_t(0)
+    assert kg.lib.kg_save_state(None, 0, C.byref(used)) == kg.KG_ESTATE
+    assert kg.lib.kg_load_state(None, 0) == kg.KG_EINVAL
+    good = _checkpoint(kg)
+    assert kg.lib.kg_load_state(good.ctypes.data, 100) == kg.KG_EINVAL
+    cases = [
+        (dict(magic=b"KGSTATE2"), kg.KG_EINVAL, "magic"),
+        (dict(version=2), kg.KG_EINVAL, "version"),
+        (dict(header_bytes=255), kg.KG_EINVAL, "header"),
+        (dict(N=17), kg.KG_ENOTSUP, "N"),
+        (dict(precision=9), kg.KG_EINVAL, "precision"),
+        (dict(dt=0.0), kg.KG_EINVAL, "range"),
+        (dict(L=float("nan")), kg.KG_EINVAL, "range"),
+        (dict(energy_every=-1), kg.KG_EINVAL, "range"),
+        (dict(level=-3), kg.KG_EINVAL, "range"),
+        (dict(frozen=2), kg.KG_EINVAL, "range"),
+        (dict(payload_bytes=8), kg.KG_EINVAL, "payload"),
+    ]
+    for over, code, word in cases:
+        b = _checkpoint(kg, **over)
+        assert kg.lib.kg_load_state(b.ctypes.data, b.size) == code, over
+        assert word in kg.last_error(), (over, kg.last_error())
+    assert kg.lib.kg_load_state(good.ctypes.data, good.size - 1) == kg.KG_EINVAL
+    assert "truncated" in kg.last_error()
+    bad = good.copy()
+    bad[kg.STATE_HEADER_BYTES + 1000] ^= 1
+    assert kg.lib.kg_load_state(bad.ctypes.data, bad.size) == kg.KG_EINVAL
+    assert "checksum" in kg.last_error()
+    # a refused checkpoint leaves the options alone
+    kg.kg_set_options(precision="mixed", energy_every=3)
+    b = _checkpoint(kg, frozen=5)
+    assert kg.lib.kg_load_state(b.ctypes.data, b.size) == kg.KG_EINVAL
+    assert kg.kg_get_options()["precision"] == kg.KG_MIXED
+    assert kg.kg_get_options()["energy_every"] == 3
+    kg.kg_set_options()
