@@ -60,6 +60,7 @@ struct Ctx {
     KgDev* dev = nullptr;
     double* part_sum = nullptr;
     double* part_max = nullptr;
+    double* part2 = nullptr;  // second-stage partial sums of the update's Q
     int nparts = 0;
     double* scal = nullptr;  // device scalars for on-demand sums
     void* tw = nullptr;      // twiddles exp(-2 pi i j/N), j < N, in the pass precision
@@ -191,10 +192,11 @@ int create_ctx(int N, double L, double dt, Ctx** out) {
     KG_TRY(dalloc(c, (void**)&c->S1, sizeof(double2) * c->nspec, "state S1"));
     KG_TRY(dalloc(c, &c->W, c->pl->store_bytes * c->nspec, "work array W"));
     KG_TRY(dalloc(c, (void**)&c->dev, sizeof(KgDev), "device state"));
-    c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->update_parts()), kLaunchF64.x_parts(N));
+    c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->update_parts(N)), kLaunchF64.x_parts(N));
     c->nparts = std::max(c->nparts, 152 * 4);
     KG_TRY(dalloc(c, (void**)&c->part_sum, sizeof(double) * c->nparts, "partials"));
     KG_TRY(dalloc(c, (void**)&c->part_max, sizeof(double) * c->nparts, "partials max"));
+    KG_TRY(dalloc(c, (void**)&c->part2, sizeof(double) * (c->nparts / 1024 + 1), "second-stage partials"));
     KG_TRY(dalloc(c, (void**)&c->scal, sizeof(double) * 8, "scalars"));
     KG_TRY(upload_tables(c));
     KG_TRY(ensure_scratch(c));
@@ -297,7 +299,7 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
     KG_CK(c->pl->col(N, -1, c->W, NH, zrs, N, c->tw, st));                        // forward z -> F^n
     if (timed) KG_CK(cudaEventRecord(c->ev[3], st));
     KG_CK(c->pl->update(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, st));
-    KG_CK(launch_fin_z(c->part_sum, c->pl->update_parts(), c->dev, q_norm, st));
+    KG_CK(launch_fin_z(c->part_sum, c->pl->update_parts(N), c->part2, c->dev, q_norm, st));
     if (timed) KG_CK(cudaEventRecord(c->ev[4], st));
     KG_CK(c->pl->col(N, +1, c->W, NH, zrs, N, c->tw, st));                        // inverse z
     if (timed) KG_CK(cudaEventRecord(c->ev[5], st));

@@ -61,8 +61,10 @@ cudaError_t launch_fin_peek(const double* ps, const double* pm, int count, KgDev
     return cudaGetLastError();
 }
 
-cudaError_t launch_fin_z(const double* ps, int count, KgDev* dev, double q_norm, cudaStream_t st) {
-    k_fin_z<<<1, kFinThreads, 0, st>>>(ps, count, dev, q_norm);
+cudaError_t launch_fin_z(const double* ps, int count, double* stage2, KgDev* dev, double q_norm, cudaStream_t st) {
+    const int n2 = (count + kSumThreads - 1) / kSumThreads;
+    k_sum_parts<<<n2, kSumThreads, 0, st>>>(ps, count, stage2, dev);
+    k_fin_z<<<1, kFinThreads, 0, st>>>(stage2, n2, dev, q_norm);
     return cudaGetLastError();
 }
 

@@ -284,69 +284,109 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
 // modes per round and issues all their loads before any arithmetic.
 // ---------------------------------------------------------------------------
 constexpr int kUpdThreads = 256;
-constexpr int kUpdItems = 4;
+constexpr int kSumThreads = 1024;   // second reduction stage of the update's Q partials
 
+// One term of Q^{n+1/2} without its constant factor 1/(2 dt^2):
+//     w_k ( |a1 - a0|^2 + r_k |a1 + a0|^2 ),   r_k = dt^2 omega_k^2 / 4,
+// (the Q definition of kg.h multiplied by 2 dt^2).  The differences and sums of the two
+// levels are formed in FP64 (a1 - a0 cancels); the squares and their sums are formed in
+// double-float on the FP32 pipe, except for the IEEE FP64 passes, which stay in FP64.
+template <class P>
+struct QTerm {
+    typedef df T;
+    static __device__ __forceinline__ T zero() { return df_make(0.f, 0.f); }
+    static __device__ __forceinline__ T term(double n_re, double n_im, double2 a, double r, bool twice) {
+        const df dre = d2df_int(n_re - a.x), dim = d2df_int(n_im - a.y);
+        const df sre = d2df_int(n_re + a.x), sim = d2df_int(n_im + a.y);
+        const df D = dre * dre + dim * dim;
+        const df S = sre * sre + sim * sim;
+        df t = D + d2df_int(r) * S;
+        return twice ? df_scale2(t, 2.0f) : t;
+    }
+    static __device__ __forceinline__ T add(T x, T y) { return x + y; }
+    static __device__ __forceinline__ T shfl_down(T x, int o) {
+        return df_make(__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o));
+    }
+    static __device__ __forceinline__ double value(T x) { return f2d_int(x.hi) + f2d_int(x.lo); }
+};
+template <>
+struct QTerm<PrecF64> {
+    typedef double T;
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T term(double n_re, double n_im, double2 a, double r, bool twice) {
+        const double dre = n_re - a.x, dim = n_im - a.y, sre = n_re + a.x, sim = n_im + a.y;
+        const double t = fma(r, fma(sre, sre, sim * sim), fma(dre, dre, dim * dim));
+        return twice ? t + t : t;
+    }
+    static __device__ __forceinline__ T add(T x, T y) { return x + y; }
+    static __device__ __forceinline__ T shfl_down(T x, int o) { return __shfl_down_sync(0xffffffffu, x, o); }
+    static __device__ __forceinline__ double value(T x) { return x; }
+};
+
+// pairwise (tree) sum of one value per thread of an NT-thread CTA; the total lands in
+// thread 0
+template <class Q, int NT>
+__device__ __forceinline__ typename Q::T block_tree_sum(typename Q::T v, typename Q::T* sm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = Q::add(v, Q::shfl_down(v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = l < NT / 32 ? sm[l] : Q::zero();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = Q::add(v, Q::shfl_down(v, o));
+    }
+    return v;
+}
+
+// Streaming per-mode update of Eq. (2) between the forward and the inverse z column
+// passes, one mode per thread (a full grid keeps enough loads in flight to stream at
+// HBM rate and lets the FP64 update overlap them):
+//     uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k        (FP64, over uh^{n-1})
+// and W <- uh^{n+1} in the pass precision for the inverse transforms.  On recording
+// steps each CTA also writes its partial sum of the Q terms (QTerm) times qc = 1/(2 dt^2).
 template <class P, int N>
-__global__ void __launch_bounds__(kUpdThreads) k_update(typename P::S* __restrict__ W, double2* S0, double2* S1,
-                                                       KgDev* __restrict__ dev, double* __restrict__ part_sum,
-                                                       const double2* __restrict__ coef,
-                                                       const double* __restrict__ w2tab, double inv_dt) {
+__global__ void __launch_bounds__(kUpdThreads, 6) k_update(typename P::S* __restrict__ W, double2* S0, double2* S1,
+                                                          KgDev* __restrict__ dev, double* __restrict__ part_sum,
+                                                          const double2* __restrict__ coef,
+                                                          const double* __restrict__ w2tab, double qr, double qc) {
     typedef typename P::R R;
+    typedef QTerm<P> Q;
     constexpr int NH = N / 2 + 1;
-    constexpr long long kModes = (long long)N * N * NH;
-    __shared__ double red[96];
+    constexpr unsigned kModes = (unsigned)N * N * NH;
+    static_assert((long long)N * N * NH < (1ll << 31), "mode indexes fit 32 bits");
+    __shared__ typename Q::T red[kUpdThreads / 32];
     const bool want_q = kg_recording(dev);
     const bool update = dev->frozen == 0;
     const double2* __restrict__ cur = dev->phase ? S1 : S0;
     double2* __restrict__ old = dev->phase ? S0 : S1;
-    NSum q;
-    q.s = 0.0;
-    q.c = 0.0;
-    const long long stride = (long long)gridDim.x * kUpdThreads * kUpdItems;
-    for (long long i0 = ((long long)blockIdx.x * kUpdThreads) * kUpdItems + threadIdx.x; i0 < kModes; i0 += stride) {
-        cx<R> f[kUpdItems];
-        double2 a[kUpdItems], b[kUpdItems], cf[kUpdItems];
-        int m2v[kUpdItems];
-        bool ok[kUpdItems];
-#pragma unroll
-        for (int t = 0; t < kUpdItems; t++) {
-            const long long i = i0 + (long long)t * kUpdThreads;
-            ok[t] = i < kModes;
-            const long long ii = ok[t] ? i : 0;
-            const int kx = (int)(ii % NH);
-            const int ky = (int)((ii / NH) % N);
-            const int kz = (int)(ii / ((long long)NH * N));
-            const int my = ky <= N / 2 ? ky : ky - N, mz = kz <= N / 2 ? kz : kz - N;
-            m2v[t] = kx * kx + my * my + mz * mz;
-            f[t] = P::load(W[ii]);
-            a[t] = cur[ii];
-            b[t] = old[ii];
-            cf[t] = __ldg(coef + m2v[t]);
-        }
-#pragma unroll
-        for (int t = 0; t < kUpdItems; t++) {
-            if (!ok[t]) continue;
-            const long long i = i0 + (long long)t * kUpdThreads;
-            const double nre = P::fma_into(cf[t].y, f[t].re, fma(cf[t].x, a[t].x, -b[t].x));
-            const double nim = P::fma_into(cf[t].y, f[t].im, fma(cf[t].x, a[t].y, -b[t].y));
-            if (update) old[i] = make_double2(nre, nim);
-            if (want_q) {
-                const int kx = (int)(i % NH);
-                const double wgt = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
-                const double dre = (nre - a[t].x) * inv_dt, dim = (nim - a[t].y) * inv_dt;
-                const double sre = nre + a[t].x, sim = nim + a[t].y;
-                q.add(wgt * (0.5 * (dre * dre + dim * dim) +
-                             0.125 * __ldg(w2tab + m2v[t]) * (sre * sre + sim * sim)));
-            }
-            W[i] = P::pack(cmake<R>(P::from_f64(nre), P::from_f64(nim)));
-        }
+    const unsigned i = blockIdx.x * kUpdThreads + threadIdx.x;
+    typename Q::T q = Q::zero();
+    if (i < kModes) {
+        const unsigned row = i / NH;
+        const int kx = (int)(i - row * NH);
+        const int ky = (int)(row % N);
+        const int kz = (int)(row / N);
+        const int my = ky <= N / 2 ? ky : ky - N, mz = kz <= N / 2 ? kz : kz - N;
+        const int m2 = kx * kx + my * my + mz * mz;
+        const cx<R> f = P::load(W[i]);
+        const double2 a = cur[i], b = old[i], cf = __ldg(coef + m2);
+        const double nre = P::fma_into(cf.y, f.re, fma(cf.x, a.x, -b.x));
+        const double nim = P::fma_into(cf.y, f.im, fma(cf.x, a.y, -b.y));
+        if (update) old[i] = make_double2(nre, nim);
+        W[i] = P::pack(cmake<R>(P::from_f64(nre), P::from_f64(nim)));
+        if (want_q) q = Q::term(nre, nim, a, qr * __ldg(w2tab + m2), kx != 0 && kx != N / 2);
     }
     if (want_q) {
-        double mx = 0.0;
-        block_reduce<kUpdThreads>(q, mx, red);
-        if (threadIdx.x == 0) part_sum[blockIdx.x] = q.value();
+        q = block_tree_sum<Q, kUpdThreads>(q, red);
+        if (threadIdx.x == 0) part_sum[blockIdx.x] = qc * Q::value(q);
     }
 }
+
+// second stage of the Q sum on recording steps: CTA b sums in[b*1024 ...] pairwise into out[b]
+__global__ void __launch_bounds__(kSumThreads) k_sum_parts(const double* __restrict__ in, int count,
+                                                           double* __restrict__ out, const KgDev* __restrict__ dev);
 
 // ---------------------------------------------------------------------------
 // finalisers (one CTA of 1024 threads)
@@ -410,6 +450,15 @@ __global__ void __launch_bounds__(kFinThreads) k_fin_peek(const double* part_sum
 }
 
 // after the z pass: Q^{l+1/2} (q_norm = h^3/N^3) and the level advance
+__global__ void __launch_bounds__(kSumThreads) k_sum_parts(const double* __restrict__ in, int count,
+                                                           double* __restrict__ out, const KgDev* __restrict__ dev) {
+    if (!kg_recording(dev)) return;
+    __shared__ double red[kSumThreads / 32];
+    const int i = blockIdx.x * kSumThreads + threadIdx.x;
+    double v = block_tree_sum<QTerm<PrecF64>, kSumThreads>(i < count ? in[i] : 0.0, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
 __global__ void __launch_bounds__(kFinThreads) k_fin_z(const double* part_sum, int count, KgDev* dev, double q_norm) {
     const bool rec = kg_recording(dev);
     NSum acc;

@@ -23,10 +23,10 @@ struct PassLaunch {
     cudaError_t (*col_from_f64)(int N, const double2* src0, const double2* src1, const KgDev* dev, void* W,
                                 size_t plane_stride, size_t row_stride, int nplanes, const void* tw, cudaStream_t st);
     // streaming FP64 update between a forward and an inverse z column pass; writes
-    // update_parts() Q partials when recording
+    // update_parts(N) Q partials when recording
     cudaError_t (*update)(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum, const double2* coef,
                           const double* w2tab, double inv_dt, cudaStream_t st);
-    int (*update_parts)();
+    int (*update_parts)(int N);
     // one persistent cooperative launch of an ensemble step (kg_ensemble.cuh)
     cudaError_t (*ens_step)(const EnsParams& p, int grid, cudaStream_t st);
     int (*ens_blocks_per_sm)();
@@ -50,7 +50,9 @@ cudaError_t launch_energy_q(int N, const double2* x, const double2* y, const dou
 cudaError_t launch_fin_x(const double* ps, const double* pm, int count, KgDev* dev, double p_norm, cudaStream_t st);
 cudaError_t launch_fin_peek(const double* ps, const double* pm, int count, KgDev* dev, double p_norm,
                             cudaStream_t st);
-cudaError_t launch_fin_z(const double* ps, int count, KgDev* dev, double q_norm, cudaStream_t st);
+// after the update: Q from its count partials (summed pairwise in blocks of 1024 into
+// stage2, which holds (count + 1023) / 1024 doubles), then the level/phase advance
+cudaError_t launch_fin_z(const double* ps, int count, double* stage2, KgDev* dev, double q_norm, cudaStream_t st);
 cudaError_t launch_fin_sum(const double* ps, int count, double norm, double* out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------

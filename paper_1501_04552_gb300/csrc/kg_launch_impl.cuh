@@ -85,11 +85,12 @@ struct Launchers {
         KG_DISPATCH_N(N, return col_from_f64_n<NN>(src0, src1, dev, W, pstride, rstride, nplanes, tw, st));
     }
 
-    static int update_parts() { return 152 * 4; }
+    static int update_parts(int N) { return (int)(((long long)N * N * (N / 2 + 1) + kUpdThreads - 1) / kUpdThreads); }
     template <int N>
     static cudaError_t update_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
                                 const double* w2, double inv_dt, cudaStream_t st) {
-        k_update<P, N><<<update_parts(), kUpdThreads, 0, st>>>((S*)W, S0, S1, dev, ps, coef, w2, inv_dt);
+        const double qr = 0.25 / (inv_dt * inv_dt), qc = 0.5 * inv_dt * inv_dt;
+        k_update<P, N><<<update_parts(N), kUpdThreads, 0, st>>>((S*)W, S0, S1, dev, ps, coef, w2, qr, qc);
         return cudaGetLastError();
     }
     static cudaError_t update(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
