@@ -192,7 +192,8 @@ int create_ctx(int N, double L, double dt, Ctx** out) {
     KG_TRY(dalloc(c, (void**)&c->S1, sizeof(double2) * c->nspec, "state S1"));
     KG_TRY(dalloc(c, &c->W, c->pl->store_bytes * c->nspec, "work array W"));
     KG_TRY(dalloc(c, (void**)&c->dev, sizeof(KgDev), "device state"));
-    c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->update_parts(N)), kLaunchF64.x_parts(N));
+    if (c->pl->x_parts(N) <= 0) KG_TRY(fail(KG_ECUDA, "x pass occupancy query failed"));
+    c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->update_parts(N)), x_inverse_parts(N));
     c->nparts = std::max(c->nparts, 152 * 4);
     KG_TRY(dalloc(c, (void**)&c->part_sum, sizeof(double) * c->nparts, "partials"));
     KG_TRY(dalloc(c, (void**)&c->part_max, sizeof(double) * c->nparts, "partials max"));
@@ -350,7 +351,7 @@ int p_from_state(Ctx* c, bool older, double* out) {
     int rc = older ? inverse_yz_f64(c, c->S1, c->S0, c->dev) : inverse_yz_f64(c, c->S0, c->S1, c->dev);
     if (rc) return rc;
     KG_CK(launch_x_inverse(N, c->tmp, nullptr, c->tw64, inv_n3(N), c->part_sum, st));
-    KG_CK(launch_fin_sum(c->part_sum, kLaunchF64.x_parts(N), c->lam * h * h * h / 4.0, c->scal, st));
+    KG_CK(launch_fin_sum(c->part_sum, x_inverse_parts(N), c->lam * h * h * h / 4.0, c->scal, st));
     KG_CK(cudaMemcpyAsync(out, c->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
     KG_CK(cudaStreamSynchronize(st));
     return KG_OK;

@@ -117,7 +117,7 @@ __device__ __forceinline__ void ens_unit(const EnsParams& p, int ii, int unit, i
         LineSmem<P> lsm{sm + li * XShape<N>::PADM};
         Stats<P> st;
         st.init();
-        x_line_body<P, N, MODE_STEP>(W + line * NH, j, lsm, tw, 1.0 / ((double)N * N * N), P::from_f64(p.lam),
+        x_line_body<P, N, MODE_STEP>(W + line * NH, W + line * NH, j, lsm, tw, 1.0 / ((double)N * N * N), P::from_f64(p.lam),
                                      false, st);
         const unsigned k2 = st.fkey();
         const unsigned wmax = __reduce_max_sync(0xffffffffu, k2);

@@ -34,6 +34,8 @@ cudaError_t launch_x_inverse(int N, const double2* in, double* u, const double2*
     });
 }
 
+int x_inverse_parts(int N) { return N * N / (kXThreads / (N / 16)); }
+
 cudaError_t launch_startup(int N, const double2* a, double2* b, const double2* f, const double2* coef, double dt,
                            cudaStream_t st) {
     KG_DISPATCH_N(N, {

@@ -21,7 +21,7 @@ struct XShape {
 };
 
 template <class P, int N>
-__device__ __forceinline__ void x_load_c2r(const typename P::S* __restrict__ line, int j, const typename P::S* __restrict__ tw,
+__device__ __forceinline__ void x_load_c2r(const typename P::S* line, int j, const typename P::S* __restrict__ tw,
                                            cx<typename P::R> (&v)[8]) {
     typedef typename P::R R;
     typedef cx<R> C;
@@ -43,16 +43,18 @@ __device__ __forceinline__ void x_load_c2r(const typename P::S* __restrict__ lin
 }
 
 // One x-line (T = N/16 threads, thread j): C2R, scale, stats, and in MODE_STEP the
-// cube, R2C and write-back.  The line is read and written through L.
+// cube, R2C and write-back.  The line is read from Lin (global memory, or the line's
+// landing slot in shared memory, which may be lsm's own storage) and written to L.
 template <class P, int N, int MODE>
-__device__ __forceinline__ void x_line_body(typename P::S* __restrict__ L, int j, LineSmem<P>& lsm,
-                                            const typename P::S* __restrict__ tw, double scale, typename P::R rlam,
-                                            bool want_sum, Stats<P>& st) {
+__device__ __forceinline__ void x_line_body(const typename P::S* Lin, typename P::S* __restrict__ L, int j,
+                                            LineSmem<P>& lsm, const typename P::S* __restrict__ tw, double scale,
+                                            typename P::R rlam, bool want_sum, Stats<P>& st) {
     typedef typename P::R R;
     typedef cx<R> C;
     constexpr int M = N / 2, T = XShape<N>::T;
     C v[8];
-    x_load_c2r<P, N>(L, j, tw, v);
+    x_load_c2r<P, N>(Lin, j, tw, v);
+    lsm.sync();   // every lane has read Lin before the first exchange writes lsm
     // inverse transform, then (stepping pass) the forward one, through one copy of the code
 #pragma unroll 1
     for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
@@ -99,25 +101,84 @@ __device__ __forceinline__ void x_line_body(typename P::S* __restrict__ L, int j
     }
 }
 
+// one element global -> shared without registers (8- or 16-byte values)
+template <class S>
+__device__ __forceinline__ void cp_async_elem(S* smem, const S* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(S) == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+    } else {
+        static_assert(sizeof(S) == 8, "8- or 16-byte elements");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    }
+}
+
+// How pass X walks W.  Pipelined (FP32 and FP64 passes, bound by latency and by the
+// FP64 pipe): a persistent grid walks the batches, and while a CTA transforms one batch
+// from shared memory the next one lands in the other half of a double buffer
+// (cp.async).  Direct (double-float passes, bound by FP32 issue, where the copy loop and
+// the extra barriers cost more than they hide): one batch per CTA, loaded from global
+// memory straight into registers.
+template <class P>
+struct XPipelined {
+    static constexpr bool value = true;
+};
+template <>
+struct XPipelined<PrecDF> {
+    static constexpr bool value = false;
+};
+
+// Pass X.  A batch is LPC consecutive x-lines, one contiguous run of LPC (N/2+1) values
+// of W; a landed batch serves as the lines' FFT exchange space.  Each CTA writes one
+// max key and (when wanted) one Sigma u^4 partial.
 template <class P, int N, int MODE>
-__global__ void __launch_bounds__(kXThreads) k_pass_x(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
+__global__ void __launch_bounds__(kXThreads, 2) k_pass_x(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
                                                       double* __restrict__ part_sum, double* __restrict__ part_max,
                                                       const typename P::S* __restrict__ tw, double scale, double lam) {
     typedef typename P::S S;
     typedef XShape<N> X;
-    constexpr int T = X::T, NH = N / 2 + 1;
+    constexpr int T = X::T, NH = N / 2 + 1, LPC = X::LPC, PADM = X::PADM;
+    constexpr int NB = N * N / LPC;     // batches
+    constexpr int CHUNK = LPC * NH;     // values of one batch
+    static_assert(PADM >= NH, "a line lands in its exchange slot");
     extern __shared__ __align__(16) unsigned char smraw[];
-    S* sm = reinterpret_cast<S*>(smraw);
+    S* buf = reinterpret_cast<S*>(smraw);   // (2 when pipelined) x LPC x PADM values
     __shared__ double red[96];
 
     const int li = threadIdx.x / T, j = threadIdx.x % T;
-    const size_t line = (size_t)blockIdx.x * X::LPC + li;
-    LineSmem<P> lsm{sm + li * X::PADM};
     const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev);
-
+    const typename P::R rlam = P::from_f64(lam);
     Stats<P> st;
     st.init();
-    x_line_body<P, N, MODE>(W + line * NH, j, lsm, tw, scale, P::from_f64(lam), want_sum, st);
+
+    if constexpr (!XPipelined<P>::value) {
+        const size_t line = (size_t)blockIdx.x * LPC + li;
+        LineSmem<P> lsm{buf + li * PADM};
+        x_line_body<P, N, MODE>(W + line * NH, W + line * NH, j, lsm, tw, scale, rlam, want_sum, st);
+    } else {
+        auto issue = [&](int batch, S* dst) {
+            const S* src = W + (size_t)batch * CHUNK;
+            for (int e = threadIdx.x; e < CHUNK; e += kXThreads) {
+                const int l = e / NH;
+                cp_async_elem(dst + l * PADM + (e - l * NH), src + e);
+            }
+        };
+        int b = blockIdx.x;
+        if (b < NB) issue(b, buf);
+        cp_async_commit();
+        for (int it = 0; b < NB; b += gridDim.x, ++it) {
+            S* cur = buf + (it & 1) * (LPC * PADM);
+            if (b + (int)gridDim.x < NB) issue(b + gridDim.x, buf + ((it + 1) & 1) * (LPC * PADM));
+            cp_async_commit();
+            cp_async_wait_1();
+            __syncthreads();
+            LineSmem<P> lsm{cur + li * PADM};
+            x_line_body<P, N, MODE>(cur + li * PADM, W + ((size_t)b * LPC + li) * NH, j, lsm, tw, scale, rlam, want_sum,
+                                    st);
+            __syncthreads();   // the buffer is the target of the copy issued next iteration
+        }
+        cp_async_wait_all();
+    }
 
     // the max every step (integer keys), the compensated FP64 sum only when it is wanted
     __shared__ unsigned long long kred[kXThreads / 32];

@@ -43,6 +43,7 @@ cudaError_t launch_x_forward(int N, const double* u, double2* out, const double2
                              cudaStream_t st);
 cudaError_t launch_x_inverse(int N, const double2* in, double* u, const double2* tw, double scale, double* part_sum,
                              cudaStream_t st);
+int x_inverse_parts(int N);   // partial sums launch_x_inverse writes
 cudaError_t launch_startup(int N, const double2* a, double2* b, const double2* f, const double2* coef, double dt,
                            cudaStream_t st);
 cudaError_t launch_energy_q(int N, const double2* x, const double2* y, const double* w2tab, double inv_dt,

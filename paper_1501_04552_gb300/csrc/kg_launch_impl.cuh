@@ -28,12 +28,43 @@ template <class P>
 struct Launchers {
     typedef typename P::S S;
 
+    // persistent x pass: as many CTAs as fit on the device at once (both modes), at most
+    // one per batch; cached per grid size
+    template <int N>
+    static size_t x_smem() {
+        typedef XShape<N> X;
+        return (size_t)(XPipelined<P>::value ? 2 : 1) * X::LPC * X::PADM * sizeof(S);
+    }
+    template <int N>
+    static int x_grid_n() {
+        static int grid = 0;
+        if (!XPipelined<P>::value) return N * N / XShape<N>::LPC;
+        if (grid == 0) {
+            typedef XShape<N> X;
+            int dev = 0, sms = 0, occ0 = 0, occ1 = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return 0;
+            if (set_smem(k_pass_x<P, N, MODE_STEP>, x_smem<N>()) != cudaSuccess ||
+                set_smem(k_pass_x<P, N, MODE_PEEK>, x_smem<N>()) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_pass_x<P, N, MODE_STEP>, kXThreads,
+                                                              x_smem<N>()) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_pass_x<P, N, MODE_PEEK>, kXThreads,
+                                                              x_smem<N>()) != cudaSuccess)
+                return 0;
+            const int occ = occ0 < occ1 ? occ0 : occ1;
+            const int nb = N * N / X::LPC;
+            grid = occ * sms < nb ? occ * sms : nb;
+            if (grid < 1) grid = 1;
+        }
+        return grid;
+    }
     template <int N>
     static cudaError_t pass_x_n(int mode, void* W, KgDev* dev, double* ps, double* pm, const void* tw, double scale,
                                 double lam, cudaStream_t st) {
-        typedef XShape<N> X;
-        const size_t smem = (size_t)X::LPC * X::PADM * sizeof(S);
-        const int grid = N * N / X::LPC;
+        const size_t smem = x_smem<N>();
+        const int grid = x_grid_n<N>();
+        if (grid == 0) return cudaErrorInvalidConfiguration;
         if (mode == MODE_STEP) {
             cudaError_t e = set_smem(k_pass_x<P, N, MODE_STEP>, smem);
             if (e != cudaSuccess) return e;
@@ -49,7 +80,10 @@ struct Launchers {
                               double scale, double lam, cudaStream_t st) {
         KG_DISPATCH_N(N, return pass_x_n<NN>(mode, W, dev, ps, pm, tw, scale, lam, st));
     }
-    static int x_parts(int N) { return N * N / (kXThreads / (N / 16)); }
+    // partials the x pass writes (its grid); 0 when the device cannot be queried
+    static int x_parts(int N) {
+        KG_DISPATCH_N(N, return x_grid_n<NN>());
+    }
 
     template <int N, int SIGN>
     static cudaError_t col_n(void* W, size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
