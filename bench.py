@@ -35,6 +35,36 @@ METRIC = "512^3 KG steps/s"
 S_BYTES = N_GRID * N_GRID * (N_GRID // 2 + 1) * 16      # one complex128 half-spectrum array
 
 
+# Table 1 of the paper: wall time (s) of 30 time steps of the same scheme at 512^3 in FP64
+# on CPU clusters (2DECOMP&FFT); quoted as context, not as a target
+PAPER_TABLE1 = [("Hornet", 12288, 0.319), ("Juqueen", 262144, 0.350), ("Stampede", 8162, 0.581),
+                ("Shaheen", 16384, 1.66), ("MareNostrum III", 64, 4.00), ("Hector", 1024, 7.66),
+                ("VSC2", 1024, 9.03), ("Beacon", 256, 9.13), ("Monte Rosa", 1024, 11.9), ("Titan", 256, 17.0),
+                ("Vedur", 1024, 18.6), ("Aquila", 256, 22.4), ("Neser", 128, 27.9)]
+
+# DRAM bytes (read + write) per launch of a step kernel at 512^3, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; the capture is summarised under
+# profiles/), valid only for the kernel sources it was taken on: KERNEL_SOURCES hashed
+TRAFFIC_512 = {}
+TRAFFIC_SOURCES_SHA = None
+KERNEL_SOURCES = ["kg_arith.cuh", "kg_fft.cuh", "kg_kernels.cuh", "kg_launch_impl.cuh"]
+
+
+def kernel_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1501_04552_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(prec, kernel, n):
+    if n != N_GRID or TRAFFIC_SOURCES_SHA is None or kernel_sources_sha() != TRAFFIC_SOURCES_SHA:
+        return None
+    return TRAFFIC_512.get((prec, kernel))
+
+
 def algorithmic_bytes(prec, n=N_GRID):
     """bytes each kernel group of a step must move (W is S or S/2 by precision, the state
     arrays are S), and the bytes an ideal step moves: four passes reading and writing W
@@ -247,7 +277,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": "k_pass_x" if names[dom] == "x" else
                 ("k_update" if names[dom] == "update" else "k_col(%s)" % names[dom]),
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "peak_kind": peak_kind,
+                "traffic": measured_traffic(prec, names[dom], NG), "peak_kind": peak_kind,
                 "step_achieved": round(step_achieved, 1), "step_frac": round(step_achieved / peak, 4),
                 "kernels": per_kernel}
     if prec == "df64":
@@ -283,9 +313,12 @@ def main():
                              "kernel_ms": {n: round(t, 4) for n, t in zip(names, o_k)},
                              "step_hbm_frac": round(o_step_bytes / (o_ms / steps * 1e-3) / 1e9 / peak, 4)}
         extras["cufft_torch"] = torch_fft_point(u0, local)
+        if NG == 512:
+            extras["paper_table1_protocol"] = {p: paper_protocol(kg, stream, torch, u0, NG, local, p)
+                                               for p in ("df64", "fp64")}
     ens = None
     if not args.no_extras and rank == 0:
-        ens = ensemble_point(kg, prec, args.ens_steps, torch, stream)
+        ens = ensemble_point(kg, prec, args.ens_steps, torch, stream, early_exit=True)
         ens["mixed"] = ensemble_point(kg, "mixed", args.ens_steps, torch, stream)
 
     base = None
@@ -315,10 +348,34 @@ def main():
     return 0
 
 
-def ensemble_point(kg, prec, steps, torch, stream):
+def paper_protocol(kg, stream, torch, u0, NG, local, prec):
+    """the paper's Table 1 protocol: device time of 30 time steps at 512^3 with no output
+    (energy recording off), placed beside the paper's 13 machines (context only)"""
+    kg.kg_set_options(precision=prec, energy_every=0)
+    d_u0 = torch.from_numpy(u0).to(f"cuda:{local}")
+    kg.kg_init_device(NG, L_BOX, DT, d_u0, None)
+    del d_u0
+    kg.kg_step(3)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kg.kg_step(30)
+    e1.record(stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    best = PAPER_TABLE1[0]
+    return {"steps": 30, "seconds": round(sec, 5), "ms_per_step": round(sec / 30 * 1e3, 3),
+            "faster_than_n_of_13": sum(1 for _, _, t in PAPER_TABLE1 if sec < t),
+            "paper_fastest": {"machine": best[0], "cores": best[1], "seconds": best[2]},
+            "ratio_to_paper_fastest": round(best[2] / sec, 2)}
+
+
+def ensemble_point(kg, prec, steps, torch, stream, early_exit=False):
     """512 instances (256 x 64^3 + 256 x 128^3, A ~ U[0.5,4], s ~ U[0.5,2], seed 4, dt = 0.005):
     one persistent launch per step vs the plain one-instance-at-a-time loop (kg_init + kg_step),
-    both for `steps` fixed steps without early exits, same precision"""
+    both for `steps` fixed steps without early exits, same precision; with early_exit also the
+    blow-up run (up to 2000 steps, max|u| > 1e3 freezes an instance, only active instance-steps
+    counted)"""
     from paper_1501_04552_gb300 import inputs as I
     Ns, A, s = I.ensemble_params(512, 4)
     kg.kg_set_options(precision=prec)
@@ -328,8 +385,17 @@ def ensemble_point(kg, prec, steps, torch, stream):
     kg.kg_ens_run(3)
     done, ms = kg.kg_ens_run(steps, 0.0)
     res = kg.kg_ens_results()
-    kg.kg_ens_finalize()
     ens_rate = float(res["level"].sum() - 3 * len(Ns)) / (ms * 1e-3)
+    blowup = None
+    if early_exit:
+        kg.kg_ens_init(Ns, L_BOX, DT, A, s)
+        bdone, bms = kg.kg_ens_run(2000, 1e3)
+        br = kg.kg_ens_results()
+        active = float(br["level"].sum())      # a frozen instance stops at its blow-up level
+        blowup = {"max_steps": 2000, "threshold": 1e3, "steps_run": int(bdone),
+                  "blown_up": int(br["frozen"].sum()), "active_instance_steps": int(active),
+                  "seconds": round(bms * 1e-3, 3), "active_instance_steps_per_s": round(active / (bms * 1e-3), 1)}
+    kg.kg_ens_finalize()
     # plain loop on a sample of the same instances
     sample = list(range(0, 256, 43)) + list(range(256, 512, 43))
     plain_steps = max(20, steps // 4)
@@ -359,7 +425,10 @@ def ensemble_point(kg, prec, steps, torch, stream):
             "speedup_vs_plain": round(ens_rate / plain_rate, 3), "precision": prec,
             "plain_loop_by_grid": plain_by_size,
             "tuned_blocks_per_sm": bps, "tuned_order": order,
-            "plain_sample": "%d instances x %d steps (kg_init + kg_step each)" % (len(sample), plain_steps)}
+            "plain_sample": "%d instances x %d steps (kg_init + kg_step each)" % (len(sample), plain_steps),
+            "blowup_run": blowup,
+            "blowup_speedup_vs_plain": (round(blowup["active_instance_steps_per_s"] / plain_rate, 3)
+                                        if blowup else None)}
 
 
 def torch_fft_point(u0, local):
