@@ -613,3 +613,275 @@ void kgo_set_num_threads(int n) {
     (void)n;
 #endif
 }
+
+/* ---------------------------------------------------------------------------
+ * Complex field (section 1.1.2 notes that the implementation allows a complex
+ * u; Eq. (1) is written with |u|^2 u).  Same scheme, same coefficients; the
+ * field is complex, so the spectrum is the full N^3 array [kz][ky][kx] with
+ * kx = 0..N-1 in FFT order, no Hermitian symmetry and no C2R rule:
+ *   nonlinearity F = lam |u|^2 u
+ *   energy       Q^{n+1/2} = (h^3/N^3) sum_k [ 1/2 |(uh^{n+1}-uh^n)/dt|^2
+ *                                         + 1/2 omega_k^2 |(uh^{n+1}+uh^n)/2|^2 ]
+ *                P^n = lam (h^3/4) sum_x |u^n|^4   (every mode has weight 1)
+ * For a real u these are the real-field definitions above (Parseval).
+ * ------------------------------------------------------------------------- */
+
+/* complex DFT along axis 0 (x), 1 (y) or 2 (z) of every line of an N^3 array */
+static int fft_axis_full(int N, cplx* a, int axis, int sign) {
+    dft_plan pl;
+    if (dft_plan_init(&pl, N, sign)) return -2;
+    int err = 0;
+    const ptrdiff_t stride = (axis == 0) ? 1 : (axis == 1) ? (ptrdiff_t)N : (ptrdiff_t)N * N;
+    const long nlines = (long)N * N;
+#pragma omp parallel
+    {
+        cplx* in = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+        cplx* out = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+        cplx* scr = (cplx*)malloc(sizeof(cplx) * (size_t)N);
+        if (!in || !out || !scr) {
+#pragma omp atomic write
+            err = -2;
+        } else {
+#pragma omp for schedule(static)
+            for (long line = 0; line < nlines; line++) {
+                long hi = line / N, lo = line % N;   /* the two indices other than the axis */
+                ptrdiff_t base;
+                if (axis == 0) base = (ptrdiff_t)line * N;                       /* (z, y) */
+                else if (axis == 1) base = (ptrdiff_t)hi * N * N + lo;           /* (z, x) */
+                else base = (ptrdiff_t)hi * N + lo;                              /* (y, x) */
+                for (int j = 0; j < N; j++) in[j] = a[base + (ptrdiff_t)j * stride];
+                dft_rec(&pl, N, in, 1, out, scr);
+                for (int j = 0; j < N; j++) a[base + (ptrdiff_t)j * stride] = out[j];
+            }
+        }
+        free(in); free(out); free(scr);
+    }
+    dft_plan_free(&pl);
+    return err;
+}
+
+/* full 3D DFT in place, unnormalised (sign -1 forward, +1 inverse) */
+int kgo_fft3d(int N, kgo_complex* a, int sign) {
+    if (N < 2 || (N & 1) || (sign != 1 && sign != -1) || !a) return -1;
+    for (int axis = 0; axis < 3; axis++) {
+        int e = fft_axis_full(N, a, axis, sign);
+        if (e) return e;
+    }
+    return 0;
+}
+
+/* k^2 of the mode stored at [kz][ky][kx] of the full spectrum */
+static double mode_k2_full(int N, double L, long kz, long ky, long kx) {
+    long mz = fft_index_to_m(kz, N), my = fft_index_to_m(ky, N), mx = fft_index_to_m(kx, N);
+    double kfac = 2.0 * KGO_PI / L;
+    double kzv = kfac * (double)mz, kyv = kfac * (double)my, kxv = kfac * (double)mx;
+    return kxv * kxv + kyv * kyv + kzv * kzv;
+}
+
+struct kgoc_state {
+    int N;
+    double L, dt, lam;
+    long level;
+    cplx* a;      /* uh^n */
+    cplx* b;      /* uh^{n-1} */
+    cplx* f;      /* scratch: u^n, then F^n, then Fh^n */
+    double last_maxabs;
+};
+
+void kgoc_destroy(kgoc_state* s) {
+    if (!s) return;
+    free(s->a); free(s->b); free(s->f);
+    free(s);
+}
+
+/* u = ifft3d(x) / N^3 into s->f */
+static int field_of(kgoc_state* s, const cplx* x) {
+    const int N = s->N;
+    const size_t n3 = (size_t)N * N * N;
+    memcpy(s->f, x, sizeof(cplx) * n3);
+    int e = kgo_fft3d(N, s->f, +1);
+    if (e) return e;
+    const double inv = 1.0 / ((double)N * (double)N * (double)N);
+#pragma omp parallel for schedule(static)
+    for (size_t i = 0; i < n3; i++) {
+        s->f[i].re *= inv;
+        s->f[i].im *= inv;
+    }
+    return 0;
+}
+
+/* s->f holds u: replace it by Fh = fft3d(lam |u|^2 u); max |u| into *maxabs */
+static int nonlinear_hat_c(kgoc_state* s, double* maxabs) {
+    const size_t n3 = (size_t)s->N * s->N * s->N;
+    double mx = 0.0;
+    const double lam = s->lam;
+#pragma omp parallel for schedule(static) reduction(max : mx)
+    for (size_t i = 0; i < n3; i++) {
+        cplx v = s->f[i];
+        double m2 = v.re * v.re + v.im * v.im;
+        double av = sqrt(m2);
+        if (av > mx || av != av) mx = (av != av) ? INFINITY : av;
+        s->f[i].re = lam * (m2 * v.re);
+        s->f[i].im = lam * (m2 * v.im);
+    }
+    if (maxabs) *maxabs = mx;
+    return kgo_fft3d(s->N, s->f, -1);
+}
+
+kgoc_state* kgoc_create(int N, double L, double dt, double lam, const kgo_complex* u0, const kgo_complex* v0) {
+    if (N < 2 || (N & 1) || !(L > 0.0) || !(dt > 0.0) || !u0) return NULL;
+    kgoc_state* s = (kgoc_state*)calloc(1, sizeof(kgoc_state));
+    if (!s) return NULL;
+    s->N = N; s->L = L; s->dt = dt; s->lam = lam; s->level = 0;
+    const size_t n3 = (size_t)N * N * N;
+    s->a = (cplx*)malloc(sizeof(cplx) * n3);
+    s->b = (cplx*)malloc(sizeof(cplx) * n3);
+    s->f = (cplx*)malloc(sizeof(cplx) * n3);
+    if (!s->a || !s->b || !s->f) { kgoc_destroy(s); return NULL; }
+    memcpy(s->a, u0, sizeof(cplx) * n3);                        /* uh^0 */
+    if (kgo_fft3d(N, s->a, -1)) { kgoc_destroy(s); return NULL; }
+    if (v0) {                                                   /* vh^0, in b for now */
+        memcpy(s->b, v0, sizeof(cplx) * n3);
+        if (kgo_fft3d(N, s->b, -1)) { kgoc_destroy(s); return NULL; }
+    } else {
+        memset(s->b, 0, sizeof(cplx) * n3);
+    }
+    memcpy(s->f, u0, sizeof(cplx) * n3);                        /* Fh^0 */
+    if (nonlinear_hat_c(s, &s->last_maxabs)) { kgoc_destroy(s); return NULL; }
+    /* uh^{-1} = c_k uh^0 - dt vh^0 + beta_k Fh^0 */
+#pragma omp parallel for schedule(static)
+    for (long kz = 0; kz < N; kz++)
+        for (long ky = 0; ky < N; ky++)
+            for (long kx = 0; kx < N; kx++) {
+                size_t i = ((size_t)kz * N + ky) * N + kx;
+                double c, beta, w2;
+                scheme_coeffs(dt, mode_k2_full(N, L, kz, ky, kx), &c, &beta, &w2);
+                cplx a0 = s->a[i], v = s->b[i], f = s->f[i];
+                s->b[i].re = c * a0.re - dt * v.re + beta * f.re;
+                s->b[i].im = c * a0.im - dt * v.im + beta * f.im;
+            }
+    return s;
+}
+
+int kgoc_step(kgoc_state* s, int nsteps, double threshold, long* blowup_level) {
+    if (!s || nsteps < 0) return -1;
+    const int N = s->N;
+    for (int it = 0; it < nsteps; it++) {
+        if (field_of(s, s->a)) return -2;                      /* u^n */
+        double mx;
+        if (nonlinear_hat_c(s, &mx)) return -2;                /* Fh^n */
+        s->last_maxabs = mx;
+        if (threshold > 0.0 && !(mx <= threshold)) {
+            if (blowup_level) *blowup_level = s->level;
+            return 1;
+        }
+#pragma omp parallel for schedule(static)
+        for (long kz = 0; kz < N; kz++)
+            for (long ky = 0; ky < N; ky++)
+                for (long kx = 0; kx < N; kx++) {
+                    size_t i = ((size_t)kz * N + ky) * N + kx;
+                    double c, beta, w2;
+                    scheme_coeffs(s->dt, mode_k2_full(N, s->L, kz, ky, kx), &c, &beta, &w2);
+                    cplx an = s->a[i], bn = s->b[i], f = s->f[i];
+                    s->b[i].re = 2.0 * c * an.re - bn.re + 2.0 * beta * f.re;
+                    s->b[i].im = 2.0 * c * an.im - bn.im + 2.0 * beta * f.im;
+                }
+        cplx* t = s->a; s->a = s->b; s->b = t;
+        s->level++;
+    }
+    return 0;
+}
+
+long kgoc_level(const kgoc_state* s) { return s ? s->level : -1; }
+double kgoc_last_maxabs(const kgoc_state* s) { return s ? s->last_maxabs : NAN; }
+
+int kgoc_fetch(kgoc_state* s, kgo_complex* u) {
+    if (!s || !u) return -1;
+    int e = field_of(s, s->a);
+    if (e) return e;
+    memcpy(u, s->f, sizeof(cplx) * (size_t)s->N * s->N * s->N);
+    return 0;
+}
+
+int kgoc_fetch_spectral(const kgoc_state* s, kgo_complex* a, kgo_complex* b) {
+    if (!s) return -1;
+    const size_t n3 = (size_t)s->N * s->N * s->N;
+    if (a) memcpy(a, s->a, sizeof(cplx) * n3);
+    if (b) memcpy(b, s->b, sizeof(cplx) * n3);
+    return 0;
+}
+
+/* Q over the full spectrum, every mode weight 1 */
+static double quadratic_energy_full(int N, double L, double dt, const cplx* x, const cplx* y) {
+    const double h = L / (double)N;
+    const double norm = h * h * h / ((double)N * (double)N * (double)N);
+    nsum total = {0.0, 0.0};
+    double* part_s = (double*)calloc((size_t)N, sizeof(double));
+    double* part_c = (double*)calloc((size_t)N, sizeof(double));
+    if (!part_s || !part_c) { free(part_s); free(part_c); return NAN; }
+#pragma omp parallel for schedule(static)
+    for (long kz = 0; kz < N; kz++) {
+        nsum acc = {0.0, 0.0};
+        for (long ky = 0; ky < N; ky++)
+            for (long kx = 0; kx < N; kx++) {
+                size_t i = ((size_t)kz * N + ky) * N + kx;
+                double c, beta, w2;
+                scheme_coeffs(dt, mode_k2_full(N, L, kz, ky, kx), &c, &beta, &w2);
+                double dre = (x[i].re - y[i].re) / dt, dim = (x[i].im - y[i].im) / dt;
+                double sre = (x[i].re + y[i].re) / 2.0, sim = (x[i].im + y[i].im) / 2.0;
+                nsum_add(&acc, 0.5 * (dre * dre + dim * dim) + 0.5 * w2 * (sre * sre + sim * sim));
+            }
+        part_s[kz] = acc.s;
+        part_c[kz] = acc.c;
+    }
+    for (long kz = 0; kz < N; kz++) { nsum_add(&total, part_s[kz]); nsum_add(&total, part_c[kz]); }
+    free(part_s); free(part_c);
+    return norm * nsum_value(&total);
+}
+
+/* P = lam (h^3/4) sum_x |u|^4 of the complex field in u */
+static double quartic_energy_c(int N, double L, double lam, const cplx* u) {
+    const double h = L / (double)N;
+    nsum total = {0.0, 0.0};
+    double* part_s = (double*)calloc((size_t)N, sizeof(double));
+    double* part_c = (double*)calloc((size_t)N, sizeof(double));
+    if (!part_s || !part_c) { free(part_s); free(part_c); return NAN; }
+    const size_t plane = (size_t)N * N;
+#pragma omp parallel for schedule(static)
+    for (long z = 0; z < N; z++) {
+        nsum acc = {0.0, 0.0};
+        for (size_t i = 0; i < plane; i++) {
+            cplx v = u[z * plane + i];
+            double m2 = v.re * v.re + v.im * v.im;
+            nsum_add(&acc, m2 * m2);
+        }
+        part_s[z] = acc.s;
+        part_c[z] = acc.c;
+    }
+    for (long z = 0; z < N; z++) { nsum_add(&total, part_s[z]); nsum_add(&total, part_c[z]); }
+    free(part_s); free(part_c);
+    return lam * (h * h * h / 4.0) * nsum_value(&total);
+}
+
+int kgoc_energy_parts(kgoc_state* s, double* Q, double* Pn, double* Pnm1) {
+    if (!s) return -1;
+    const int N = s->N;
+    if (Q) *Q = quadratic_energy_full(N, s->L, s->dt, s->a, s->b);
+    if (Pn) {
+        if (field_of(s, s->a)) return -2;
+        *Pn = quartic_energy_c(N, s->L, s->lam, s->f);
+    }
+    if (Pnm1) {
+        if (field_of(s, s->b)) return -2;
+        *Pnm1 = quartic_energy_c(N, s->L, s->lam, s->f);
+    }
+    return 0;
+}
+
+int kgoc_energy(kgoc_state* s, double* E) {
+    double Q, Pn, Pm;
+    int e = kgoc_energy_parts(s, &Q, &Pn, &Pm);
+    if (e) return e;
+    *E = Q - 0.5 * (Pn + Pm);
+    return 0;
+}

@@ -56,6 +56,20 @@ int kgo_energy(kgo_state* s, double* E);                                 /* E^{n
 int kgo_energy_initial(int N, double L, double lam, const double* u0, const double* v0, double* E);
 int kgo_shell_energies(int N, double L, const double* u0, double* out4);
 
+/* complex field (full N^3 spectrum [kz][ky][kx], kx in FFT order; F = lam |u|^2 u;
+ * every mode has weight 1 in Q; P = lam (h^3/4) sum |u|^4).  u0, v0, u: N^3 complex */
+typedef struct kgoc_state kgoc_state;
+int kgo_fft3d(int N, kgo_complex* a, int sign);                        /* in place, unnormalised */
+kgoc_state* kgoc_create(int N, double L, double dt, double lam, const kgo_complex* u0, const kgo_complex* v0);
+void kgoc_destroy(kgoc_state* s);
+int kgoc_step(kgoc_state* s, int nsteps, double threshold, long* blowup_level);
+long kgoc_level(const kgoc_state* s);
+double kgoc_last_maxabs(const kgoc_state* s);
+int kgoc_fetch(kgoc_state* s, kgo_complex* u);
+int kgoc_fetch_spectral(const kgoc_state* s, kgo_complex* a, kgo_complex* b);
+int kgoc_energy_parts(kgoc_state* s, double* Q, double* Pn, double* Pnm1);
+int kgoc_energy(kgoc_state* s, double* E);
+
 int kgo_num_threads(void);
 void kgo_set_num_threads(int n);
 

@@ -45,6 +45,19 @@ def lib():
         L.kgo_energy.argtypes = [vp, dp]
         L.kgo_energy_initial.argtypes = [C.c_int, C.c_double, C.c_double, vp, vp, dp]
         L.kgo_shell_energies.argtypes = [C.c_int, C.c_double, vp, vp]
+        L.kgo_fft3d.argtypes = [C.c_int, vp, C.c_int]
+        L.kgoc_create.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, vp, vp]
+        L.kgoc_create.restype = vp
+        L.kgoc_destroy.argtypes = [vp]
+        L.kgoc_step.argtypes = [vp, C.c_int, C.c_double, C.POINTER(C.c_long)]
+        L.kgoc_level.argtypes = [vp]
+        L.kgoc_level.restype = C.c_long
+        L.kgoc_last_maxabs.argtypes = [vp]
+        L.kgoc_last_maxabs.restype = C.c_double
+        L.kgoc_fetch.argtypes = [vp, vp]
+        L.kgoc_fetch_spectral.argtypes = [vp, vp, vp]
+        L.kgoc_energy_parts.argtypes = [vp, dp, dp, dp]
+        L.kgoc_energy.argtypes = [vp, dp]
         L.kgo_num_threads.restype = C.c_int
         L.kgo_set_num_threads.argtypes = [C.c_int]
         _lib = L
@@ -203,4 +216,73 @@ class Solver:
     def energy(self):
         E = C.c_double()
         _check(lib().kgo_energy(self._s, C.byref(E)), "energy")
+        return E.value
+
+
+def fft3d(a, sign=-1):
+    """full complex 3D DFT of an N^3 array (unnormalised), returns a copy"""
+    a = np.array(a, dtype=np.complex128, order="C", copy=True)
+    _check(lib().kgo_fft3d(a.shape[0], _p(a), sign), "fft3d")
+    return a
+
+
+class ComplexSolver:
+    """FP64 oracle for a complex field u (F = lam |u|^2 u): Eq. (2) on the full N^3
+    spectrum (the complex-field reading of section 1.1.2); same interface as Solver"""
+
+    def __init__(self, N, L, dt, u0, v0=None, lam=1.0):
+        u0 = np.ascontiguousarray(u0, dtype=np.complex128)
+        assert u0.shape == (N, N, N)
+        v = None if v0 is None else np.ascontiguousarray(v0, dtype=np.complex128)
+        self.N, self.L, self.dt, self.lam = N, L, dt, lam
+        self._s = lib().kgoc_create(N, L, dt, lam, _p(u0), None if v is None else _p(v))
+        if not self._s:
+            raise RuntimeError("oracle kgoc_create failed")
+
+    def close(self):
+        if self._s:
+            lib().kgoc_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n, threshold=0.0):
+        lvl = C.c_long(-1)
+        rc = lib().kgoc_step(self._s, int(n), float(threshold), C.byref(lvl))
+        if rc < 0:
+            raise RuntimeError("oracle kgoc_step failed with code %d" % rc)
+        return rc == 1, lvl.value
+
+    @property
+    def level(self):
+        return lib().kgoc_level(self._s)
+
+    @property
+    def last_maxabs(self):
+        return lib().kgoc_last_maxabs(self._s)
+
+    def fetch(self):
+        out = np.empty((self.N,) * 3, dtype=np.complex128)
+        _check(lib().kgoc_fetch(self._s, _p(out)), "fetch")
+        return out
+
+    def spectral(self):
+        N = self.N
+        a = np.empty((N, N, N), dtype=np.complex128)
+        b = np.empty_like(a)
+        _check(lib().kgoc_fetch_spectral(self._s, _p(a), _p(b)), "fetch_spectral")
+        return a, b
+
+    def energy_parts(self):
+        Q, Pn, Pm = C.c_double(), C.c_double(), C.c_double()
+        _check(lib().kgoc_energy_parts(self._s, C.byref(Q), C.byref(Pn), C.byref(Pm)), "energy_parts")
+        return Q.value, Pn.value, Pm.value
+
+    def energy(self):
+        E = C.c_double()
+        _check(lib().kgoc_energy(self._s, C.byref(E)), "energy")
         return E.value
