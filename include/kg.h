@@ -117,6 +117,29 @@ int kg_step_timed(int n, float* ms);
 /* Bytes of device memory the context holds. */
 int kg_memory(size_t* bytes);
 
+/* ---- complex field (section 1.1.2: the paper's implementation allows a complex u) ----
+ * The same scheme for complex u with the nonlinearity lam |u|^2 u (Eq. (1) as printed):
+ * the spectrum is the full N^3 array [kz][ky][kx] with kx = 0..N-1 in FFT order (no
+ * Hermitian symmetry, no C2R rule), every mode has weight 1 in Q, P^n = lam (h^3/4)
+ * sum |u^n|^4, and the blow-up check and kg_status use max |u^n| = max sqrt(re^2 + im^2).
+ * kg_step, kg_energy, kg_status, kg_fetch_spectral (N^3 complex values each),
+ * kg_step_timed, kg_save_state and kg_load_state work on either kind of context;
+ * kg_fetch / kg_fetch_device refuse a complex one (KG_ESTATE) and the calls below
+ * refuse a real one. */
+
+/* As kg_init for a complex field: u0, v0 (v0 may be NULL) are host pointers to N^3
+ * complex values, interleaved re/im (2 N^3 doubles), [z][y][x] with x fastest. */
+int kg_init_complex(int N, double L, double dt, const double* u0, const double* v0);
+
+/* As kg_init_complex with device pointers. */
+int kg_init_complex_device(int N, double L, double dt, const double* d_u0, const double* d_v0);
+
+/* Synchronise and write the complex u^n (2 N^3 doubles, interleaved) to host memory. */
+int kg_fetch_complex(double* u);
+
+/* Same into caller-owned device memory (2 N^3 doubles); enqueued, no host sync. */
+int kg_fetch_complex_device(double* d_u);
+
 /* ---- checkpoint / resume (the paper has no counterpart; long blow-up runs need it) ----
  * A checkpoint is one host byte buffer: a kg_state_header followed by the payload,
  * uh^n then uh^{n-1} (N*N*(N/2+1) complex doubles each, interleaved re/im,
@@ -142,9 +165,11 @@ typedef struct kg_state_header {
     long long Q_last_level;
     int have_E0, pad0;
     double E0;                   /* the drift watchdog's first energy */
-    unsigned long long payload_bytes;   /* 2 * 16 * N*N*(N/2+1) */
+    unsigned long long payload_bytes;   /* 2 * 16 * N*N*(N/2+1) (complex field: 2 * 16 * N^3) */
     unsigned long long checksum;        /* kg_state_checksum of the payload */
-    unsigned char reserved[256 - 160];  /* zero */
+    int complex_field;                  /* 1: complex field (payload 2 * 16 * N^3 bytes) */
+    int pad1;
+    unsigned char reserved[256 - 168];  /* zero */
 } kg_state_header;
 
 /* Write the current context into h (cap bytes).  *used receives the checkpoint

@@ -48,6 +48,7 @@ int g_alloc_counter = 0;
 
 struct Ctx {
     int N = 0, NH = 0, prec = KG_DF64;
+    bool cplx = false;       // complex field: full N^3 spectrum, N columns per plane
     double L = 0, dt = 0, lam = 1.0;
     size_t nspec = 0, nphys = 0;   // complex values per spectral array, reals per physical array
     cudaStream_t own_stream = nullptr;
@@ -136,6 +137,11 @@ int ensure_scratch(Ctx* c) {
 int inverse_yz_f64(Ctx* c, const double2* src0, const double2* src1, const KgDev* sel) {
     const int N = c->N, NH = c->NH;
     cudaStream_t st = stream_of(c);
+    if (c->cplx) {
+        KG_CK(kLaunchF64.colc_from_f64(N, src0, src1, sel, c->tmp, N, (size_t)N * N, N, c->tw64, st));   // z
+        KG_CK(kLaunchF64.colc(N, +1, c->tmp, (size_t)N * N, N, N, c->tw64, st));                        // y
+        return KG_OK;
+    }
     KG_CK(kLaunchF64.col_from_f64(N, src0, src1, sel, c->tmp, NH, (size_t)N * NH, N, c->tw64, st));   // z
     KG_CK(kLaunchF64.col(N, +1, c->tmp, (size_t)N * NH, NH, N, c->tw64, st));                         // y
     return KG_OK;
@@ -159,7 +165,7 @@ int check_grid(int N, double L, double dt) {
 
 // a context for an N^3 run in the current options, with every buffer a step needs;
 // replaces (destroys) the previous context first.  On failure nothing is kept.
-int create_ctx(int N, double L, double dt, Ctx** out) {
+int create_ctx(int N, double L, double dt, bool cplx, Ctx** out) {
     if (g_ctx) {
         destroy(g_ctx);
         g_ctx = nullptr;
@@ -173,8 +179,9 @@ int create_ctx(int N, double L, double dt, Ctx** out) {
     c->lam = g_opt.nonlinearity;
     c->prec = g_opt.precision;
     c->pl = launcher(c->prec);
-    c->nspec = (size_t)N * N * c->NH;
-    c->nphys = (size_t)N * N * N;
+    c->cplx = cplx;
+    c->nspec = (size_t)N * N * (cplx ? N : c->NH);
+    c->nphys = (size_t)N * N * N * (cplx ? 2 : 1);   // doubles of one physical field
     int rc = KG_OK;
 #define KG_TRY(x)              \
     do {                       \
@@ -192,8 +199,12 @@ int create_ctx(int N, double L, double dt, Ctx** out) {
     KG_TRY(dalloc(c, (void**)&c->S1, sizeof(double2) * c->nspec, "state S1"));
     KG_TRY(dalloc(c, &c->W, c->pl->store_bytes * c->nspec, "work array W"));
     KG_TRY(dalloc(c, (void**)&c->dev, sizeof(KgDev), "device state"));
-    if (c->pl->x_parts(N) <= 0) KG_TRY(fail(KG_ECUDA, "x pass occupancy query failed"));
-    c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->update_parts(N)), x_inverse_parts(N));
+    if (cplx) {
+        c->nparts = std::max(std::max(c->pl->xc_parts(N), c->pl->updatec_parts(N)), xc_inverse_parts(N));
+    } else {
+        if (c->pl->x_parts(N) <= 0) KG_TRY(fail(KG_ECUDA, "x pass occupancy query failed"));
+        c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->update_parts(N)), x_inverse_parts(N));
+    }
     c->nparts = std::max(c->nparts, 152 * 4);
     KG_TRY(dalloc(c, (void**)&c->part_sum, sizeof(double) * c->nparts, "partials"));
     KG_TRY(dalloc(c, (void**)&c->part_max, sizeof(double) * c->nparts, "partials max"));
@@ -235,7 +246,7 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
         if (rc) return rc;
     }
     Ctx* c = nullptr;
-    rc = create_ctx(N, L, dt, &c);
+    rc = create_ctx(N, L, dt, false, &c);
     if (rc) return rc;
 #define KG_TRY(x)              \
     do {                       \
@@ -282,6 +293,67 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
     return KG_OK;
 }
 
+// complex field: u0, v0 are N^3 complex values (2 N^3 doubles, interleaved re/im)
+int init_common_c(int N, double L, double dt, const double* u0, const double* v0, bool device_ptrs) {
+    int rc = check_grid(N, L, dt);
+    if (rc) return rc;
+    if (!u0) return fail(KG_EINVAL, "u0 is NULL");
+    const size_t n3 = (size_t)N * N * N;
+    if (!device_ptrs) {
+        rc = check_finite(u0, 2 * n3, "u0");
+        if (!rc && v0) rc = check_finite(v0, 2 * n3, "v0");
+        if (rc) return rc;
+    }
+    Ctx* c = nullptr;
+    rc = create_ctx(N, L, dt, true, &c);
+    if (rc) return rc;
+    cudaStream_t st = stream_of(c);
+    double2* fbuf = nullptr;
+    double2* extra = nullptr;
+    if (c->pl->store_bytes == sizeof(double2)) {
+        fbuf = (double2*)c->W;
+    } else {
+        rc = dalloc(c, (void**)&extra, sizeof(double2) * c->nspec, "set-up scratch");
+        if (rc) {
+            destroy(c);
+            return rc;
+        }
+        fbuf = extra;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->phys, u0, sizeof(double2) * n3,
+                                    device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        destroy(c);
+        return fail(KG_ECUDA, std::string("copy u0: ") + cudaGetErrorString(e));
+    }
+    Tables tb{c->tw, c->tw64, c->coef, c->w2};
+    rc = init_state_c(N, c->prec, dt, c->lam, tb, (double2*)c->phys, (const double2*)v0, device_ptrs, c->S0, c->S1,
+                      c->W, fbuf, st);
+    KgDev d = fresh_dev();
+    d.complex_field = 1;
+    if (!rc && cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = fail(KG_ECUDA, "dev upload");
+    if (!rc) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(KG_ECUDA, std::string("init: ") + cudaGetErrorString(e));
+    }
+    if (rc) {
+        destroy(c);
+        return rc;
+    }
+    if (extra) {
+        cudaFree(extra);
+        for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
+            if (*it == extra) {
+                c->allocs.erase(it);
+                break;
+            }
+        c->bytes -= sizeof(double2) * c->nspec;
+    }
+    g_ctx = c;
+    return KG_OK;
+}
+
 // one step; with timed, CUDA events split it into six kernel groups and ms[0..5]
 // accumulate their device times: x pass (+ its finaliser), forward y, forward z, update
 // (+ its finaliser), inverse z, inverse y
@@ -290,21 +362,34 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
     const double h = c->L / N;
     const double p_norm = c->lam * h * h * h / 4.0;
     const double q_norm = h * h * h * inv_n3(N);
-    const size_t yps = (size_t)N * NH, zrs = (size_t)N * NH;
+    // column geometry: NX columns per plane (N/2 + 1, or N for a complex field)
+    const int NX = c->cplx ? N : NH;
+    const size_t yps = (size_t)N * NX, zrs = (size_t)N * NX;
+    auto col = c->cplx ? c->pl->colc : c->pl->col;
     if (timed) KG_CK(cudaEventRecord(c->ev[0], st));
-    KG_CK(c->pl->pass_x(N, MODE_STEP, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
-    KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->x_parts(N), c->dev, p_norm, st));
+    if (c->cplx) {
+        KG_CK(c->pl->passc_x(N, MODE_STEP, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
+        KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->xc_parts(N), c->dev, p_norm, st));
+    } else {
+        KG_CK(c->pl->pass_x(N, MODE_STEP, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
+        KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->x_parts(N), c->dev, p_norm, st));
+    }
     if (timed) KG_CK(cudaEventRecord(c->ev[1], st));
-    KG_CK(c->pl->col(N, -1, c->W, yps, NH, N, c->tw, st));                        // forward y
+    KG_CK(col(N, -1, c->W, yps, NX, N, c->tw, st));                               // forward y
     if (timed) KG_CK(cudaEventRecord(c->ev[2], st));
-    KG_CK(c->pl->col(N, -1, c->W, NH, zrs, N, c->tw, st));                        // forward z -> F^n
+    KG_CK(col(N, -1, c->W, NX, zrs, N, c->tw, st));                               // forward z -> F^n
     if (timed) KG_CK(cudaEventRecord(c->ev[3], st));
-    KG_CK(c->pl->update(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, st));
-    KG_CK(launch_fin_z(c->part_sum, c->pl->update_parts(N), c->part2, c->dev, q_norm, st));
+    if (c->cplx) {
+        KG_CK(c->pl->updatec(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, st));
+        KG_CK(launch_fin_z(c->part_sum, c->pl->updatec_parts(N), c->part2, c->dev, q_norm, st));
+    } else {
+        KG_CK(c->pl->update(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, st));
+        KG_CK(launch_fin_z(c->part_sum, c->pl->update_parts(N), c->part2, c->dev, q_norm, st));
+    }
     if (timed) KG_CK(cudaEventRecord(c->ev[4], st));
-    KG_CK(c->pl->col(N, +1, c->W, NH, zrs, N, c->tw, st));                        // inverse z
+    KG_CK(col(N, +1, c->W, NX, zrs, N, c->tw, st));                               // inverse z
     if (timed) KG_CK(cudaEventRecord(c->ev[5], st));
-    KG_CK(c->pl->col(N, +1, c->W, yps, NH, N, c->tw, st));                        // inverse y
+    KG_CK(col(N, +1, c->W, yps, NX, N, c->tw, st));                               // inverse y
     if (timed) {
         KG_CK(cudaEventRecord(c->ev[6], st));
         KG_CK(cudaEventSynchronize(c->ev[6]));
@@ -350,8 +435,13 @@ int p_from_state(Ctx* c, bool older, double* out) {
     // phase 0: S0 current; the "older" array is the other one
     int rc = older ? inverse_yz_f64(c, c->S1, c->S0, c->dev) : inverse_yz_f64(c, c->S0, c->S1, c->dev);
     if (rc) return rc;
-    KG_CK(launch_x_inverse(N, c->tmp, nullptr, c->tw64, inv_n3(N), c->part_sum, st));
-    KG_CK(launch_fin_sum(c->part_sum, x_inverse_parts(N), c->lam * h * h * h / 4.0, c->scal, st));
+    if (c->cplx) {
+        KG_CK(launch_xc_inverse(N, c->tmp, nullptr, c->tw64, inv_n3(N), c->part_sum, st));
+        KG_CK(launch_fin_sum(c->part_sum, xc_inverse_parts(N), c->lam * h * h * h / 4.0, c->scal, st));
+    } else {
+        KG_CK(launch_x_inverse(N, c->tmp, nullptr, c->tw64, inv_n3(N), c->part_sum, st));
+        KG_CK(launch_fin_sum(c->part_sum, x_inverse_parts(N), c->lam * h * h * h / 4.0, c->scal, st));
+    }
     KG_CK(cudaMemcpyAsync(out, c->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
     KG_CK(cudaStreamSynchronize(st));
     return KG_OK;
@@ -429,7 +519,7 @@ int kg_energy(double* E) {
         const double2* cur = d.phase ? c->S1 : c->S0;
         const double2* old = d.phase ? c->S0 : c->S1;
         const int np = 152 * 4;
-        KG_CK(launch_energy_q(N, cur, old, c->w2, 1.0 / c->dt, c->part_sum, np, st));
+        KG_CK(launch_energy_q(N, cur, old, c->w2, 1.0 / c->dt, c->part_sum, np, c->cplx, st));
         KG_CK(launch_fin_sum(c->part_sum, np, h * h * h * inv_n3(N), c->scal, st));
         KG_CK(cudaMemcpyAsync(&Q, c->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
         KG_CK(cudaStreamSynchronize(st));
@@ -443,8 +533,17 @@ int kg_energy(double* E) {
     }
     // P^n: from W (which holds the yz-inverse of uh^n) unless the state froze
     if (!d.frozen) {
-        KG_CK(c->pl->pass_x(N, MODE_PEEK, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
-        KG_CK(launch_fin_peek(c->part_sum, c->part_max, c->pl->x_parts(N), c->dev, c->lam * h * h * h / 4.0, st));
+        if (c->cplx) {
+            KG_CK(c->pl->passc_x(N, MODE_PEEK, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam,
+                                 st));
+            KG_CK(launch_fin_peek(c->part_sum, c->part_max, c->pl->xc_parts(N), c->dev, c->lam * h * h * h / 4.0,
+                                  st));
+        } else {
+            KG_CK(c->pl->pass_x(N, MODE_PEEK, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam,
+                                st));
+            KG_CK(launch_fin_peek(c->part_sum, c->part_max, c->pl->x_parts(N), c->dev, c->lam * h * h * h / 4.0,
+                                  st));
+        }
         KgDev d2;
         rc = read_dev(c, &d2);
         if (rc) return rc;
@@ -467,6 +566,7 @@ int kg_fetch_device(double* d_u) {
     Ctx* c = g_ctx;
     if (!c) return fail(KG_ESTATE, "kg_fetch before kg_init");
     if (!d_u) return fail(KG_EINVAL, "output pointer is NULL");
+    if (c->cplx) return fail(KG_ESTATE, "the context holds a complex field: use kg_fetch_complex");
     int rc = inverse_yz_f64(c, c->S0, c->S1, c->dev);
     if (rc) return rc;
     KG_CK(launch_x_inverse(c->N, c->tmp, d_u, c->tw64, inv_n3(c->N), nullptr, stream_of(c)));
@@ -477,7 +577,40 @@ int kg_fetch(double* u) {
     Ctx* c = g_ctx;
     if (!c) return fail(KG_ESTATE, "kg_fetch before kg_init");
     if (!u) return fail(KG_EINVAL, "output pointer is NULL");
+    if (c->cplx) return fail(KG_ESTATE, "the context holds a complex field: use kg_fetch_complex");
     int rc = kg_fetch_device(c->phys);
+    if (rc) return rc;
+    cudaStream_t st = stream_of(c);
+    KG_CK(cudaMemcpyAsync(u, c->phys, sizeof(double) * c->nphys, cudaMemcpyDeviceToHost, st));
+    KG_CK(cudaStreamSynchronize(st));
+    return KG_OK;
+}
+
+int kg_init_complex(int N, double L, double dt, const double* u0, const double* v0) {
+    return init_common_c(N, L, dt, u0, v0, false);
+}
+
+int kg_init_complex_device(int N, double L, double dt, const double* d_u0, const double* d_v0) {
+    return init_common_c(N, L, dt, d_u0, d_v0, true);
+}
+
+int kg_fetch_complex_device(double* d_u) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_fetch_complex before kg_init_complex");
+    if (!d_u) return fail(KG_EINVAL, "output pointer is NULL");
+    if (!c->cplx) return fail(KG_ESTATE, "the context holds a real field: use kg_fetch");
+    int rc = inverse_yz_f64(c, c->S0, c->S1, c->dev);
+    if (rc) return rc;
+    KG_CK(launch_xc_inverse(c->N, c->tmp, (double2*)d_u, c->tw64, inv_n3(c->N), nullptr, stream_of(c)));
+    return KG_OK;
+}
+
+int kg_fetch_complex(double* u) {
+    Ctx* c = g_ctx;
+    if (!c) return fail(KG_ESTATE, "kg_fetch_complex before kg_init_complex");
+    if (!u) return fail(KG_EINVAL, "output pointer is NULL");
+    if (!c->cplx) return fail(KG_ESTATE, "the context holds a real field: use kg_fetch");
+    int rc = kg_fetch_complex_device(c->phys);
     if (rc) return rc;
     cudaStream_t st = stream_of(c);
     KG_CK(cudaMemcpyAsync(u, c->phys, sizeof(double) * c->nphys, cudaMemcpyDeviceToHost, st));
@@ -610,6 +743,7 @@ int kg_save_state(void* h, size_t cap, size_t* used) {
     hd.Q_last_level = d.Q_last_level;
     hd.have_E0 = c->have_E0 ? 1 : 0;
     hd.E0 = c->E0;
+    hd.complex_field = c->cplx ? 1 : 0;
     hd.payload_bytes = 2 * arr;
     unsigned char* base = (unsigned char*)h;
     cudaStream_t st = stream_of(c);
@@ -635,9 +769,11 @@ int kg_load_state(const void* h, size_t len) {
     if (!launcher(hd.precision)) return fail(KG_EINVAL, "checkpoint precision unknown");
     if (!(hd.L > 0.0) || !std::isfinite(hd.L) || !(hd.dt > 0.0) || !std::isfinite(hd.dt) ||
         !std::isfinite(hd.nonlinearity) || !std::isfinite(hd.blowup_threshold) || !std::isfinite(hd.drift_tol) ||
-        hd.energy_every < 0 || hd.level < 0 || (hd.frozen != 0 && hd.frozen != 1))
+        hd.energy_every < 0 || hd.level < 0 || (hd.frozen != 0 && hd.frozen != 1) ||
+        (hd.complex_field != 0 && hd.complex_field != 1))
         return fail(KG_EINVAL, "checkpoint header field out of range");
-    const size_t nspec = (size_t)hd.N * hd.N * (hd.N / 2 + 1);
+    const bool cplx = hd.complex_field == 1;
+    const size_t nspec = (size_t)hd.N * hd.N * (cplx ? hd.N : hd.N / 2 + 1);
     const size_t arr = sizeof(double2) * nspec;
     if (hd.payload_bytes != 2 * arr) return fail(KG_EINVAL, "checkpoint payload size does not match N");
     if (len < sizeof(hd) + 2 * arr) return fail(KG_EINVAL, "checkpoint truncated");
@@ -652,9 +788,9 @@ int kg_load_state(const void* h, size_t len) {
     o.drift_tol = hd.drift_tol;
     g_opt = o;
     Ctx* c = nullptr;
-    int rc = create_ctx(hd.N, hd.L, hd.dt, &c);
+    int rc = create_ctx(hd.N, hd.L, hd.dt, cplx, &c);
     if (rc) return rc;
-    const int N = c->N, NH = c->NH;
+    const int N = c->N, NX = cplx ? N : c->NH;
     cudaStream_t st = stream_of(c);
     KgDev d = fresh_dev();
     d.level = hd.level;
@@ -665,12 +801,15 @@ int kg_load_state(const void* h, size_t len) {
     d.P_last_level = hd.P_last_level;
     d.Q_last = hd.Q_last;
     d.Q_last_level = hd.Q_last_level;
+    d.complex_field = cplx ? 1 : 0;
     cudaError_t e = cudaMemcpyAsync(c->S0, base + sizeof(hd), arr, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->S1, base + sizeof(hd) + arr, arr, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st);
     // W = the yz inverse of uh^n in the pass precision, as the last two transforms of a step leave it
-    if (e == cudaSuccess) e = c->pl->col_from_f64(N, c->S0, c->S1, nullptr, c->W, NH, (size_t)N * NH, N, c->tw, st);
-    if (e == cudaSuccess) e = c->pl->col(N, +1, c->W, (size_t)N * NH, NH, N, c->tw, st);
+    auto col = cplx ? c->pl->colc : c->pl->col;
+    auto col_f64 = cplx ? c->pl->colc_from_f64 : c->pl->col_from_f64;
+    if (e == cudaSuccess) e = col_f64(N, c->S0, c->S1, nullptr, c->W, NX, (size_t)N * NX, N, c->tw, st);
+    if (e == cudaSuccess) e = col(N, +1, c->W, (size_t)N * NX, NX, N, c->tw, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         destroy(c);

@@ -1,0 +1,166 @@
+// kg_complex.cuh -- x-direction kernels for a complex field u (section 1.1.2: the
+// paper's implementation allows a complex field; Eq. (1) has the nonlinearity |u|^2 u).
+//
+// The spectrum is the full N^3 array [kz][ky][kx] (kx = 0..N-1 in FFT order), so the
+// x direction is a plain complex transform of N points per line: no real-to-complex
+// packing, no C2R rule.  The y and z passes are the column kernels of the real field
+// with N columns per plane instead of N/2 + 1.
+#pragma once
+#include "kg_kernels.cuh"
+
+namespace kg {
+
+template <int N>
+struct XcShape {
+    static constexpr int T = N / 8;             // threads per x-line
+    static constexpr int LPC = kXThreads / T;   // lines per CTA
+    static constexpr int PADN = N + N / 8;      // padded shared-memory slots per line
+    static constexpr bool CTA_SYNC = T > 32;    // a line spans more than one warp
+    static_assert(kXThreads % T == 0, "whole lines per CTA");
+};
+
+// one line's exchange space; a line wider than a warp synchronises the CTA (every
+// thread of the CTA runs the same transform, so the barrier is reached by all)
+template <class P, bool CTA>
+struct LineSmemX {
+    typename P::S* base;
+    static __device__ __forceinline__ int pad(int i) { return i + (i >> 3); }
+    __device__ __forceinline__ void put(int i, cx<typename P::R> v) { base[pad(i)] = P::pack(v); }
+    __device__ __forceinline__ cx<typename P::R> get(int i) const { return P::load(base[pad(i)]); }
+    __device__ __forceinline__ void sync() const {
+        if (CTA) __syncthreads();
+        else __syncwarp();
+    }
+};
+
+// Pass X of a complex field.  MODE_STEP: per x-line, inverse transform, scale 1/N^3 ->
+// u^n; |u|^2 keys and (when wanted) sum |u|^4; F = lam |u|^2 u; forward transform;
+// written back in place.  MODE_PEEK: inverse transform and the statistics only.
+template <class P, int N, int MODE>
+__global__ void __launch_bounds__(kXThreads, 2) k_pass_xc(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
+                                                         double* __restrict__ part_sum, double* __restrict__ part_max,
+                                                         const typename P::S* __restrict__ tw, double scale,
+                                                         double lam) {
+    typedef typename P::S S;
+    typedef typename P::R R;
+    typedef cx<R> C;
+    typedef XcShape<N> X;
+    constexpr int T = X::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    S* sm = reinterpret_cast<S*>(smraw);
+    __shared__ double red[96];
+
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const size_t line = (size_t)blockIdx.x * X::LPC + li;
+    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN};
+    const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev);
+    const R rlam = P::from_f64(lam);
+    S* __restrict__ L = W + line * N;
+    Stats<P> st;
+    st.init();
+
+    C v[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) v[s] = P::load(L[j + T * s]);
+    fft<P, N>(v, j, tw, 1, lsm, +1);
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        v[s].re = P::scale2(v[s].re, scale);   // scale = 1/N^3, a power of two
+        v[s].im = P::scale2(v[s].im, scale);
+        const R m2 = v[s].re * v[s].re + v[s].im * v[s].im;
+        st.take_sq(m2, want_sum);
+        if (MODE == MODE_STEP) {
+            const R g = rlam * m2;
+            v[s].re = g * v[s].re;
+            v[s].im = g * v[s].im;
+        }
+    }
+    if (MODE == MODE_STEP) {
+        fft<P, N>(v, j, tw, 1, lsm, -1);
+#pragma unroll
+        for (int s = 0; s < 8; s++) L[j + T * s] = P::pack(v[s]);
+    }
+
+    __shared__ unsigned long long kred[kXThreads / 32];
+    const unsigned long long key = block_max_key<kXThreads>(st.dkey(), kred);
+    if (threadIdx.x == 0) part_max[blockIdx.x] = __longlong_as_double((long long)key);
+    if (want_sum) {
+        NSum acc;
+        acc.s = st.total();
+        acc.c = 0.0;
+        double unused = 0.0;
+        block_reduce<kXThreads>(acc, unused, red);
+        if (threadIdx.x == 0) part_sum[blockIdx.x] = acc.value();
+    }
+}
+
+// FP64 set-up: forward transform along x of complex physical lines,
+// out[line][k] = sum_x f(u[line][x]) e^{-2 pi i k x / N}, f(u) = u or lam |u|^2 u
+template <int N>
+__global__ void __launch_bounds__(kXThreads) k_xc_forward(const double2* __restrict__ u, double2* __restrict__ out,
+                                                          const double2* __restrict__ tw, int cube, double lam) {
+    typedef PrecF64 P;
+    typedef XcShape<N> X;
+    constexpr int T = X::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double2* sm = reinterpret_cast<double2*>(smraw);
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const size_t line = (size_t)blockIdx.x * X::LPC + li;
+    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN};
+    cx<double> v[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        double2 z = u[line * N + j + T * s];
+        if (cube) {
+            const double g = lam * (z.x * z.x + z.y * z.y);
+            z = make_double2(g * z.x, g * z.y);
+        }
+        v[s] = cmake<double>(z.x, z.y);
+    }
+    fft<P, N>(v, j, tw, 1, lsm, -1);
+#pragma unroll
+    for (int s = 0; s < 8; s++) out[line * N + j + T * s] = make_double2(v[s].re, v[s].im);
+}
+
+// FP64 read-out: inverse transform along x, times scale, into u (may be NULL);
+// optionally the per-CTA sum of |u|^4
+template <int N>
+__global__ void __launch_bounds__(kXThreads) k_xc_inverse(const double2* __restrict__ in, double2* __restrict__ u,
+                                                          const double2* __restrict__ tw, double scale,
+                                                          double* __restrict__ part_sum) {
+    typedef PrecF64 P;
+    typedef XcShape<N> X;
+    constexpr int T = X::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double2* sm = reinterpret_cast<double2*>(smraw);
+    __shared__ double red[96];
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const size_t line = (size_t)blockIdx.x * X::LPC + li;
+    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN};
+    cx<double> v[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        const double2 z = in[line * N + j + T * s];
+        v[s] = cmake<double>(z.x, z.y);
+    }
+    fft<P, N>(v, j, tw, 1, lsm, +1);
+    NSum acc;
+    acc.s = 0.0;
+    acc.c = 0.0;
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        const double a = v[s].re * scale, b = v[s].im * scale;
+        if (u) u[line * N + j + T * s] = make_double2(a, b);
+        if (part_sum) {
+            const double m2 = a * a + b * b;
+            acc.add(m2 * m2);
+        }
+    }
+    if (part_sum) {
+        double mx = 0.0;
+        block_reduce<kXThreads>(acc, mx, red);
+        if (threadIdx.x == 0) part_sum[blockIdx.x] = acc.value();
+    }
+}
+
+}  // namespace kg

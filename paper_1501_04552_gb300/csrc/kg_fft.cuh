@@ -280,6 +280,12 @@ struct Stats<PrecF64> {
             sum.add(u2 * u2);
         }
     }
+    // complex field: m2 = |u|^2 >= 0; the key is |u|^2 and the sum takes |u|^4
+    __device__ __forceinline__ void take_sq(double m2, bool want_sum) {
+        const unsigned long long key = (unsigned long long)__double_as_longlong(m2);
+        mx = key > mx ? key : mx;
+        if (want_sum) sum.add(m2 * m2);
+    }
     __device__ __forceinline__ double total() const { return sum.value(); }
     __device__ __forceinline__ double maxval() const { return __longlong_as_double((long long)mx); }
     // float bits of max|u| (nan above inf above every finite value)
@@ -303,6 +309,12 @@ struct Stats<PrecDF> {
             acc = acc + u2 * u2;
         }
     }
+    // complex field: m2 = |u|^2 >= 0; the key is |u|^2 and the sum takes |u|^4
+    __device__ __forceinline__ void take_sq(df m2, bool want_sum) {
+        const unsigned int key = __float_as_uint(m2.hi);
+        mx = key > mx ? key : mx;
+        if (want_sum) acc = acc + m2 * m2;
+    }
     __device__ __forceinline__ double total() const { return f2d_int(acc.hi) + f2d_int(acc.lo); }
     __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
     __device__ __forceinline__ unsigned fkey() const { return mx; }
@@ -324,6 +336,11 @@ struct Stats<PrecF32> {
             acc = acc + df_make(u2 * u2, 0.f);
         }
     }
+    __device__ __forceinline__ void take_sq(float m2, bool want_sum) {
+        const unsigned int key = __float_as_uint(m2);
+        mx = key > mx ? key : mx;
+        if (want_sum) acc = acc + df_make(m2 * m2, 0.f);
+    }
     __device__ __forceinline__ double total() const { return f2d_int(acc.hi) + f2d_int(acc.lo); }
     __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
     __device__ __forceinline__ unsigned fkey() const { return mx; }
@@ -342,7 +359,7 @@ struct KgDev {
     int frozen;               // blow-up flag
     long long blowup_level;   // level at which the state froze
     int energy_every;         // record Q, P on steps from level l with (l+1) % energy_every == 0
-    int pad0;
+    int complex_field;        // 1: complex u; the x pass max keys are |u|^2
     double threshold;         // > 0: blow-up check max|u^n| > threshold
     double maxabs_last;       // max |u^l| of the last x pass of a step
     double P_last;            // P^l of the last recording step

@@ -25,6 +25,14 @@ int forward3d(int N, const double* u, double2* out, const double2* tw64, int cub
     KG_HCK(kLaunchF64.col(N, -1, out, NH, (size_t)N * NH, N, tw64, st));   // z
     return KG_OK;
 }
+// FP64 forward 3D transform of a complex physical device array (full spectrum);
+// cube: of lam |u|^2 u instead of u
+int forward3d_c(int N, const double2* u, double2* out, const double2* tw64, int cube, double lam, cudaStream_t st) {
+    KG_HCK(launch_xc_forward(N, u, out, tw64, cube, lam, st));
+    KG_HCK(kLaunchF64.colc(N, -1, out, (size_t)N * N, N, N, tw64, st));   // y
+    KG_HCK(kLaunchF64.colc(N, -1, out, N, (size_t)N * N, N, tw64, st));   // z
+    return KG_OK;
+}
 }  // namespace
 
 const PassLaunch* launcher_for(int prec) {
@@ -101,9 +109,30 @@ int init_state(int N, int prec, double dt, double lam, const Tables& tb, double*
     } else {
         KG_HCK(cudaMemsetAsync(S1, 0, sizeof(double2) * nspec, st));
     }
-    KG_HCK(launch_startup(N, S0, S1, fbuf, tb.coef, dt, st));    // S1 = uh^{-1}
+    KG_HCK(launch_startup(N, S0, S1, fbuf, tb.coef, dt, false, st));    // S1 = uh^{-1}
     KG_HCK(pl->col_from_f64(N, S0, S1, nullptr, W, NH, (size_t)N * NH, N, tb.tw, st));   // z inverse of uh^0
     KG_HCK(pl->col(N, +1, W, (size_t)N * NH, NH, N, tb.tw, st));                          // y inverse
+    return KG_OK;
+}
+
+int init_state_c(int N, int prec, double dt, double lam, const Tables& tb, double2* phys, const double2* v0,
+                 bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st) {
+    const size_t n3 = (size_t)N * N * N;
+    const PassLaunch* pl = launcher_for(prec);
+    if (!pl) return set_last_error(KG_EINVAL, "unknown precision");
+    int rc = forward3d_c(N, phys, fbuf, tb.tw64, 1, lam, st);   // F^0 = FFT(lam |u0|^2 u0)
+    if (!rc) rc = forward3d_c(N, phys, S0, tb.tw64, 0, lam, st);  // uh^0
+    if (rc) return rc;
+    if (v0) {
+        KG_HCK(cudaMemcpyAsync(phys, v0, sizeof(double2) * n3, v0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        rc = forward3d_c(N, phys, S1, tb.tw64, 0, lam, st);       // vh^0
+        if (rc) return rc;
+    } else {
+        KG_HCK(cudaMemsetAsync(S1, 0, sizeof(double2) * n3, st));
+    }
+    KG_HCK(launch_startup(N, S0, S1, fbuf, tb.coef, dt, true, st));       // S1 = uh^{-1}
+    KG_HCK(pl->colc_from_f64(N, S0, S1, nullptr, W, N, (size_t)N * N, N, tb.tw, st));   // z inverse of uh^0
+    KG_HCK(pl->colc(N, +1, W, (size_t)N * N, N, N, tb.tw, st));                         // y inverse
     return KG_OK;
 }
 

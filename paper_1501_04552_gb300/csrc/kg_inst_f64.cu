@@ -5,7 +5,8 @@
 namespace kg {
 template struct Launchers<PrecF64>;
 const PassLaunch kLaunchF64 = {
-    &Launchers<PrecF64>::pass_x, &Launchers<PrecF64>::col, &Launchers<PrecF64>::col_from_f64, &Launchers<PrecF64>::update, &Launchers<PrecF64>::update_parts, &Launchers<PrecF64>::ens_step, &Launchers<PrecF64>::ens_blocks_per_sm, &Launchers<PrecF64>::x_parts, sizeof(PrecF64::S)};
+    &Launchers<PrecF64>::pass_x, &Launchers<PrecF64>::col, &Launchers<PrecF64>::col_from_f64, &Launchers<PrecF64>::update, &Launchers<PrecF64>::update_parts, &Launchers<PrecF64>::ens_step, &Launchers<PrecF64>::ens_blocks_per_sm, &Launchers<PrecF64>::x_parts, sizeof(PrecF64::S),
+    &Launchers<PrecF64>::passc_x, &Launchers<PrecF64>::xc_parts, &Launchers<PrecF64>::colc, &Launchers<PrecF64>::colc_from_f64, &Launchers<PrecF64>::updatec, &Launchers<PrecF64>::updatec_parts};
 }  // namespace kg
 
 namespace kg {
@@ -37,20 +38,48 @@ cudaError_t launch_x_inverse(int N, const double2* in, double* u, const double2*
 int x_inverse_parts(int N) { return N * N / (kXThreads / (N / 16)); }
 
 cudaError_t launch_startup(int N, const double2* a, double2* b, const double2* f, const double2* coef, double dt,
-                           cudaStream_t st) {
+                           bool cplx, cudaStream_t st) {
     KG_DISPATCH_N(N, {
-        k_startup<NN><<<152 * 8, 256, 0, st>>>(a, b, f, coef, dt);
+        if (cplx) k_startup<NN, true><<<152 * 8, 256, 0, st>>>(a, b, f, coef, dt);
+        else k_startup<NN, false><<<152 * 8, 256, 0, st>>>(a, b, f, coef, dt);
         return cudaGetLastError();
     });
 }
 
 cudaError_t launch_energy_q(int N, const double2* x, const double2* y, const double* w2tab, double inv_dt,
-                            double* part_sum, int nparts, cudaStream_t st) {
+                            double* part_sum, int nparts, bool cplx, cudaStream_t st) {
     KG_DISPATCH_N(N, {
-        k_energy_q<NN><<<nparts, 256, 0, st>>>(x, y, w2tab, inv_dt, part_sum);
+        if (cplx) k_energy_q<NN, true><<<nparts, 256, 0, st>>>(x, y, w2tab, inv_dt, part_sum);
+        else k_energy_q<NN, false><<<nparts, 256, 0, st>>>(x, y, w2tab, inv_dt, part_sum);
         return cudaGetLastError();
     });
 }
+
+cudaError_t launch_xc_forward(int N, const double2* u, double2* out, const double2* tw, int cube, double lam,
+                              cudaStream_t st) {
+    KG_DISPATCH_N(N, {
+        typedef XcShape<NN> X;
+        const size_t smem = (size_t)X::LPC * X::PADN * sizeof(double2);
+        cudaError_t e = set_smem(k_xc_forward<NN>, smem);
+        if (e != cudaSuccess) return e;
+        k_xc_forward<NN><<<NN * NN / X::LPC, kXThreads, smem, st>>>(u, out, tw, cube, lam);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_xc_inverse(int N, const double2* in, double2* u, const double2* tw, double scale,
+                              double* part_sum, cudaStream_t st) {
+    KG_DISPATCH_N(N, {
+        typedef XcShape<NN> X;
+        const size_t smem = (size_t)X::LPC * X::PADN * sizeof(double2);
+        cudaError_t e = set_smem(k_xc_inverse<NN>, smem);
+        if (e != cudaSuccess) return e;
+        k_xc_inverse<NN><<<NN * NN / X::LPC, kXThreads, smem, st>>>(in, u, tw, scale, part_sum);
+        return cudaGetLastError();
+    });
+}
+
+int xc_inverse_parts(int N) { return N * N / (kXThreads / (N / 8)); }
 
 cudaError_t launch_fin_x(const double* ps, const double* pm, int count, KgDev* dev, double p_norm, cudaStream_t st) {
     k_fin_x<<<1, kFinThreads, 0, st>>>(ps, pm, count, dev, p_norm);

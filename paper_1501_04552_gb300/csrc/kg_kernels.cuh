@@ -226,28 +226,29 @@ __device__ __forceinline__ void col_body(const typename Pin::S* src, typename Po
     }
 }
 
-template <class Pin, class P, class Pout, int N, int SIGN>
+// NC columns per plane: N/2 + 1 (half spectrum of a real field) or N (complex field)
+template <class Pin, class P, class Pout, int N, int SIGN, int NC = N / 2 + 1>
 __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col(const typename Pin::S* src, typename Pout::S* dst,
                                                                size_t plane_stride, size_t row_stride,
                                                                const typename P::S* __restrict__ tw) {
-    constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
+    constexpr int C = ColShape<P>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
     const int c = threadIdx.x % C, j = threadIdx.x / C;
     const int kx = blockIdx.x * C + c;
     ColSmem<P, C> csm{sm, c};
     tw = stage_table(tw, sm + N * C, N);
-    col_body<Pin, P, Pout, N, SIGN>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NH, j, csm, tw);
+    col_body<Pin, P, Pout, N, SIGN>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NC, j, csm, tw);
 }
 
 // inverse column FFT from an FP64 spectral array into W (precision P); the source is
 // src1 when dev != NULL and dev->phase == 1, src0 otherwise (the current level's array)
-template <class P, int N>
+template <class P, int N, int NC = N / 2 + 1>
 __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col_sel(const double2* src0, const double2* src1,
                                                                    const KgDev* dev, typename P::S* dst,
                                                                    size_t plane_stride, size_t row_stride,
                                                                    const typename P::S* __restrict__ tw) {
-    constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
+    constexpr int C = ColShape<P>::C;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
     const double2* src = (dev != nullptr && dev->phase) ? src1 : src0;
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col_sel(const double
     const int kx = blockIdx.x * C + c;
     ColSmem<P, C> csm{sm, c};
     tw = stage_table(tw, sm + N * C, N);
-    col_body<PrecF64, P, P, N, +1>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NH, j, csm, tw);
+    col_body<PrecF64, P, P, N, +1>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NC, j, csm, tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,6 +345,29 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
 // update and the Q terms are those of z_body.  Each thread takes kUpdItems consecutive
 // modes per round and issues all their loads before any arithmetic.
 // ---------------------------------------------------------------------------
+// The mode stored at index i of a spectral array: the half spectrum of a real field
+// ([kz][ky][kx], kx = 0..N/2) or the full spectrum of a complex field (kx = 0..N-1 in
+// FFT order).  m2 = mx^2 + my^2 + mz^2 indexes the coefficient tables; w is the
+// Parseval weight of the mode in the energy sums.
+template <int N, bool CPLX>
+struct ModeIndex {
+    static constexpr int NX = CPLX ? N : N / 2 + 1;
+    static constexpr long long kModes = (long long)N * N * NX;
+    static_assert(kModes < (1ll << 31), "mode indexes fit 32 bits");
+    int m2;
+    bool twice;
+    __device__ __forceinline__ explicit ModeIndex(unsigned i) {
+        const unsigned row = i / NX;
+        const int kx = (int)(i - row * NX);
+        const int ky = (int)(row % N);
+        const int kz = (int)(row / N);
+        const int mx = (CPLX && kx > N / 2) ? kx - N : kx;
+        const int my = ky <= N / 2 ? ky : ky - N, mz = kz <= N / 2 ? kz : kz - N;
+        m2 = mx * mx + my * my + mz * mz;
+        twice = !CPLX && kx != 0 && kx != N / 2;
+    }
+};
+
 constexpr int kUpdThreads = 256;
 constexpr int kSumThreads = 1024;   // second reduction stage of the update's Q partials
 
@@ -407,16 +431,16 @@ __device__ __forceinline__ typename Q::T block_tree_sum(typename Q::T v, typenam
 //     uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k        (FP64, over uh^{n-1})
 // and W <- uh^{n+1} in the pass precision for the inverse transforms.  On recording
 // steps each CTA also writes its partial sum of the Q terms (QTerm) times qc = 1/(2 dt^2).
-template <class P, int N>
+template <class P, int N, bool CPLX = false>
 __global__ void __launch_bounds__(kUpdThreads, 6) k_update(typename P::S* __restrict__ W, double2* S0, double2* S1,
                                                           KgDev* __restrict__ dev, double* __restrict__ part_sum,
                                                           const double2* __restrict__ coef,
                                                           const double* __restrict__ w2tab, double qr, double qc) {
     typedef typename P::R R;
     typedef QTerm<P> Q;
-    constexpr int NH = N / 2 + 1;
-    constexpr unsigned kModes = (unsigned)N * N * NH;
-    static_assert((long long)N * N * NH < (1ll << 31), "mode indexes fit 32 bits");
+    typedef ModeIndex<N, CPLX> MI;
+    constexpr unsigned kModes = (unsigned)MI::kModes;
+    static_assert(MI::kModes < (1ll << 31), "mode indexes fit 32 bits");
     __shared__ typename Q::T red[kUpdThreads / 32];
     const bool want_q = kg_recording(dev);
     const bool update = dev->frozen == 0;
@@ -425,19 +449,14 @@ __global__ void __launch_bounds__(kUpdThreads, 6) k_update(typename P::S* __rest
     const unsigned i = blockIdx.x * kUpdThreads + threadIdx.x;
     typename Q::T q = Q::zero();
     if (i < kModes) {
-        const unsigned row = i / NH;
-        const int kx = (int)(i - row * NH);
-        const int ky = (int)(row % N);
-        const int kz = (int)(row / N);
-        const int my = ky <= N / 2 ? ky : ky - N, mz = kz <= N / 2 ? kz : kz - N;
-        const int m2 = kx * kx + my * my + mz * mz;
+        const MI mi((unsigned)i);
         const cx<R> f = P::load(W[i]);
-        const double2 a = cur[i], b = old[i], cf = __ldg(coef + m2);
+        const double2 a = cur[i], b = old[i], cf = __ldg(coef + mi.m2);
         const double nre = P::fma_into(cf.y, f.re, fma(cf.x, a.x, -b.x));
         const double nim = P::fma_into(cf.y, f.im, fma(cf.x, a.y, -b.y));
         if (update) old[i] = make_double2(nre, nim);
         W[i] = P::pack(cmake<R>(P::from_f64(nre), P::from_f64(nim)));
-        if (want_q) q = Q::term(nre, nim, a, qr * __ldg(w2tab + m2), kx != 0 && kx != N / 2);
+        if (want_q) q = Q::term(nre, nim, a, qr * __ldg(w2tab + mi.m2), mi.twice);
     }
     if (want_q) {
         q = block_tree_sum<Q, kUpdThreads>(q, red);
@@ -483,6 +502,7 @@ __global__ void __launch_bounds__(kFinThreads) k_fin_x(const double* part_sum, c
     NSum acc;
     double mx;
     fin_reduce(kg_recording(dev) ? part_sum : nullptr, part_max, count, acc, mx);
+    if (dev->complex_field) mx = sqrt(mx);   // the keys were |u|^2
     if (threadIdx.x == 0) {
         if (!dev->frozen) {
             dev->maxabs_last = mx;
@@ -504,6 +524,7 @@ __global__ void __launch_bounds__(kFinThreads) k_fin_peek(const double* part_sum
     NSum acc;
     double mx;
     fin_reduce(part_sum, part_max, count, acc, mx);
+    if (dev->complex_field) mx = sqrt(mx);
     if (threadIdx.x == 0) {
         dev->P_peek = p_norm * acc.value();
         dev->maxabs_peek = mx;
@@ -628,17 +649,13 @@ __global__ void __launch_bounds__(kXThreads) k_x_inverse(const double2* __restri
 }
 
 // uh^{-1} = c_k uh^0 - dt vh^0 + beta_k F^0 (coef holds 2c, 2 beta); b holds vh^0 on entry
-template <int N>
+template <int N, bool CPLX = false>
 __global__ void k_startup(const double2* __restrict__ a, double2* __restrict__ b, const double2* __restrict__ f,
                           const double2* __restrict__ coef, double dt) {
-    constexpr int NH = N / 2 + 1;
-    const size_t total = (size_t)N * N * NH;
+    typedef ModeIndex<N, CPLX> MI;
+    const size_t total = (size_t)MI::kModes;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(i % NH);
-        const int ky = (int)((i / NH) % N);
-        const int kz = (int)(i / ((size_t)NH * N));
-        const int my = ky <= N / 2 ? ky : ky - N, mz = kz <= N / 2 ? kz : kz - N;
-        const double2 cf = coef[kx * kx + my * my + mz * mz];
+        const double2 cf = coef[MI((unsigned)i).m2];
         const double c = 0.5 * cf.x, beta = 0.5 * cf.y;
         const double2 a0 = a[i], v0 = b[i], f0 = f[i];
         b[i] = make_double2(c * a0.x - dt * v0.x + beta * f0.x, c * a0.y - dt * v0.y + beta * f0.y);
@@ -646,26 +663,23 @@ __global__ void k_startup(const double2* __restrict__ a, double2* __restrict__ b
 }
 
 // Q(x, y) partials for arbitrary FP64 spectral pairs (energy outside the recorded steps)
-template <int N>
+template <int N, bool CPLX = false>
 __global__ void __launch_bounds__(256) k_energy_q(const double2* __restrict__ x, const double2* __restrict__ y,
                                                   const double* __restrict__ w2tab, double inv_dt,
                                                   double* __restrict__ part_sum) {
-    constexpr int NH = N / 2 + 1;
+    typedef ModeIndex<N, CPLX> MI;
     __shared__ double red[96];
-    const size_t total = (size_t)N * N * NH;
+    const size_t total = (size_t)MI::kModes;
     NSum acc;
     acc.s = 0.0;
     acc.c = 0.0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(i % NH);
-        const int ky = (int)((i / NH) % N);
-        const int kz = (int)(i / ((size_t)NH * N));
-        const int my = ky <= N / 2 ? ky : ky - N, mz = kz <= N / 2 ? kz : kz - N;
-        const double w = (kx == 0 || kx == N / 2) ? 1.0 : 2.0;
+        const MI mi((unsigned)i);
+        const double w = mi.twice ? 2.0 : 1.0;
         const double2 a = x[i], b = y[i];
         const double dre = (a.x - b.x) * inv_dt, dim = (a.y - b.y) * inv_dt;
         const double sre = a.x + b.x, sim = a.y + b.y;
-        acc.add(w * (0.5 * (dre * dre + dim * dim) + 0.125 * w2tab[kx * kx + my * my + mz * mz] * (sre * sre + sim * sim)));
+        acc.add(w * (0.5 * (dre * dre + dim * dim) + 0.125 * w2tab[mi.m2] * (sre * sre + sim * sim)));
     }
     double mx = 0.0;
     block_reduce<256>(acc, mx, red);

@@ -32,6 +32,18 @@ struct PassLaunch {
     int (*ens_blocks_per_sm)();
     int (*x_parts)(int N);
     size_t store_bytes;  // bytes of one complex value of W
+    // complex field (full N^3 spectrum, N columns per plane): x pass, column FFTs,
+    // column FFT from an FP64 source, update, and their partial counts
+    cudaError_t (*passc_x)(int N, int mode, void* W, KgDev* dev, double* part_sum, double* part_max, const void* tw,
+                           double scale, double lam, cudaStream_t st);
+    int (*xc_parts)(int N);
+    cudaError_t (*colc)(int N, int sign, void* W, size_t plane_stride, size_t row_stride, int nplanes, const void* tw,
+                        cudaStream_t st);
+    cudaError_t (*colc_from_f64)(int N, const double2* src0, const double2* src1, const KgDev* dev, void* W,
+                                 size_t plane_stride, size_t row_stride, int nplanes, const void* tw, cudaStream_t st);
+    cudaError_t (*updatec)(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum,
+                           const double2* coef, const double* w2tab, double inv_dt, cudaStream_t st);
+    int (*updatec_parts)(int N);
 };
 
 extern const PassLaunch kLaunchF64;
@@ -44,10 +56,18 @@ cudaError_t launch_x_forward(int N, const double* u, double2* out, const double2
 cudaError_t launch_x_inverse(int N, const double2* in, double* u, const double2* tw, double scale, double* part_sum,
                              cudaStream_t st);
 int x_inverse_parts(int N);   // partial sums launch_x_inverse writes
+// cplx: full N^3 spectrum of a complex field instead of the half spectrum
 cudaError_t launch_startup(int N, const double2* a, double2* b, const double2* f, const double2* coef, double dt,
-                           cudaStream_t st);
+                           bool cplx, cudaStream_t st);
 cudaError_t launch_energy_q(int N, const double2* x, const double2* y, const double* w2tab, double inv_dt,
-                            double* part_sum, int nparts, cudaStream_t st);
+                            double* part_sum, int nparts, bool cplx, cudaStream_t st);
+// complex field, FP64: forward transform along x (u -> out; cube: of lam |u|^2 u) and
+// inverse transform along x times scale (u may be NULL; part_sum: per-CTA sum |u|^4)
+cudaError_t launch_xc_forward(int N, const double2* u, double2* out, const double2* tw, int cube, double lam,
+                              cudaStream_t st);
+cudaError_t launch_xc_inverse(int N, const double2* in, double2* u, const double2* tw, double scale,
+                              double* part_sum, cudaStream_t st);
+int xc_inverse_parts(int N);
 cudaError_t launch_fin_x(const double* ps, const double* pm, int count, KgDev* dev, double p_norm, cudaStream_t st);
 cudaError_t launch_fin_peek(const double* ps, const double* pm, int count, KgDev* dev, double p_norm,
                             cudaStream_t st);
@@ -77,6 +97,11 @@ int make_tables(int N, int prec, double L, double dt, const AllocFn& alloc, Tabl
 // precision; fbuf is an FP64 spectral scratch (may alias W when W holds 16-byte values)
 int init_state(int N, int prec, double dt, double lam, const Tables& tb, double* phys, const double* v0,
                bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st);
+
+// the same for a complex field: phys and v0 hold N^3 complex values, S0, S1, W and fbuf
+// the full N^3 spectrum
+int init_state_c(int N, int prec, double dt, double lam, const Tables& tb, double2* phys, const double2* v0,
+                 bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st);
 
 // record a failure for kg_last_error(); returns code
 int set_last_error(int code, const std::string& msg);

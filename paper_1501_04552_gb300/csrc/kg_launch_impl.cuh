@@ -1,5 +1,6 @@
 // kg_launch_impl.cuh -- template launchers, instantiated once per precision.
 #pragma once
+#include "kg_complex.cuh"
 #include "kg_ensemble.cuh"
 #include "kg_kernels.cuh"
 #include "kg_launch.h"
@@ -85,14 +86,14 @@ struct Launchers {
         KG_DISPATCH_N(N, return x_grid_n<NN>());
     }
 
-    template <int N, int SIGN>
+    template <int N, int SIGN, int NC = N / 2 + 1>
     static cudaError_t col_n(void* W, size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
-        constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
+        constexpr int C = ColShape<P>::C;
         const size_t smem = (size_t)(N * C + N) * sizeof(S);
-        auto kern = k_col<P, P, P, N, SIGN>;
+        auto kern = k_col<P, P, P, N, SIGN, NC>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        dim3 grid((NH + C - 1) / C, nplanes);
+        dim3 grid((NC + C - 1) / C, nplanes);
         kern<<<grid, C * N / 8, smem, st>>>((const S*)W, (S*)W, pstride, rstride, (const S*)tw);
         return cudaGetLastError();
     }
@@ -102,15 +103,15 @@ struct Launchers {
         KG_DISPATCH_N(N, return (col_n<NN, +1>(W, pstride, rstride, nplanes, tw, st)));
     }
 
-    template <int N>
+    template <int N, int NC = N / 2 + 1>
     static cudaError_t col_from_f64_n(const double2* src0, const double2* src1, const KgDev* dev, void* W,
                                       size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
-        constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
+        constexpr int C = ColShape<P>::C;
         const size_t smem = (size_t)(N * C + N) * sizeof(S);
-        auto kern = k_col_sel<P, N>;
+        auto kern = k_col_sel<P, N, NC>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
-        dim3 grid((NH + C - 1) / C, nplanes);
+        dim3 grid((NC + C - 1) / C, nplanes);
         kern<<<grid, C * N / 8, smem, st>>>(src0, src1, dev, (S*)W, pstride, rstride, (const S*)tw);
         return cudaGetLastError();
     }
@@ -131,6 +132,49 @@ struct Launchers {
                               const double* w2, double inv_dt, cudaStream_t st) {
         KG_DISPATCH_N(N, return update_n<NN>(W, S0, S1, dev, ps, coef, w2, inv_dt, st));
     }
+    // ---- complex field ----
+    template <int N>
+    static cudaError_t passc_x_n(int mode, void* W, KgDev* dev, double* ps, double* pm, const void* tw,
+                                 double scale, double lam, cudaStream_t st) {
+        typedef XcShape<N> X;
+        const size_t smem = (size_t)X::LPC * X::PADN * sizeof(S);
+        const int grid = N * N / X::LPC;
+        if (mode == MODE_STEP) {
+            cudaError_t e = set_smem(k_pass_xc<P, N, MODE_STEP>, smem);
+            if (e != cudaSuccess) return e;
+            k_pass_xc<P, N, MODE_STEP><<<grid, kXThreads, smem, st>>>((S*)W, dev, ps, pm, (const S*)tw, scale, lam);
+        } else {
+            cudaError_t e = set_smem(k_pass_xc<P, N, MODE_PEEK>, smem);
+            if (e != cudaSuccess) return e;
+            k_pass_xc<P, N, MODE_PEEK><<<grid, kXThreads, smem, st>>>((S*)W, dev, ps, pm, (const S*)tw, scale, lam);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t passc_x(int N, int mode, void* W, KgDev* dev, double* ps, double* pm, const void* tw,
+                               double scale, double lam, cudaStream_t st) {
+        KG_DISPATCH_N(N, return passc_x_n<NN>(mode, W, dev, ps, pm, tw, scale, lam, st));
+    }
+    static int xc_parts(int N) { return N * N / (kXThreads / (N / 8)); }
+    static cudaError_t colc(int N, int sign, void* W, size_t pstride, size_t rstride, int nplanes, const void* tw,
+                            cudaStream_t st) {
+        if (sign < 0) { KG_DISPATCH_N(N, return (col_n<NN, -1, NN>(W, pstride, rstride, nplanes, tw, st))); }
+        KG_DISPATCH_N(N, return (col_n<NN, +1, NN>(W, pstride, rstride, nplanes, tw, st)));
+    }
+    static cudaError_t colc_from_f64(int N, const double2* src0, const double2* src1, const KgDev* dev, void* W,
+                                     size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
+        KG_DISPATCH_N(N, return (col_from_f64_n<NN, NN>(src0, src1, dev, W, pstride, rstride, nplanes, tw, st)));
+    }
+    static int updatec_parts(int N) { return (int)(((long long)N * N * N + kUpdThreads - 1) / kUpdThreads); }
+    static cudaError_t updatec(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
+                               const double* w2, double inv_dt, cudaStream_t st) {
+        const double qr = 0.25 / (inv_dt * inv_dt), qc = 0.5 * inv_dt * inv_dt;
+        KG_DISPATCH_N(N, {
+            k_update<P, NN, true><<<updatec_parts(NN), kUpdThreads, 0, st>>>((S*)W, S0, S1, dev, ps, coef, w2, qr,
+                                                                             qc);
+            return cudaGetLastError();
+        });
+    }
+
     static size_t ens_smem() {
         typedef EnsUnits<P, 64> U64;
         typedef EnsUnits<P, 128> U128;

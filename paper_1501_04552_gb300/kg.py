@@ -69,6 +69,10 @@ _sig = {
     "kg_fetch_spectral": ([_vp, _vp], C.c_int),
     "kg_step_timed": ([C.c_int, C.POINTER(C.c_float)], C.c_int),
     "kg_memory": ([C.POINTER(C.c_size_t)], C.c_int),
+    "kg_init_complex": ([C.c_int, C.c_double, C.c_double, _vp, _vp], C.c_int),
+    "kg_init_complex_device": ([C.c_int, C.c_double, C.c_double, _vp, _vp], C.c_int),
+    "kg_fetch_complex": ([_vp], C.c_int),
+    "kg_fetch_complex_device": ([_vp], C.c_int),
     "kg_save_state": ([_vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
     "kg_load_state": ([_vp, C.c_size_t], C.c_int),
     "kg_state_checksum": ([_vp, C.c_size_t], C.c_ulonglong),
@@ -136,11 +140,48 @@ def kg_init(N, L, dt, u0, v0=None):
     v = None if v0 is None else _host(v0, N ** 3, "v0")
     _check(lib.kg_init(N, L, dt, u.ctypes.data, None if v is None else v.ctypes.data), "kg_init")
     _state["N"] = N
+    _state["cplx"] = False
 
 
 def kg_init_device(N, L, dt, d_u0, d_v0=None):
     _check(lib.kg_init_device(N, L, dt, _dptr(d_u0), _dptr(d_v0)), "kg_init_device")
     _state["N"] = N
+    _state["cplx"] = False
+
+
+def _host_c(a, n3, name):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if a.size != n3:
+        raise ValueError("%s must hold N^3 = %d complex values" % (name, n3))
+    return a
+
+
+def kg_init_complex(N, L, dt, u0, v0=None):
+    """complex field: u0, v0 are N^3 complex arrays ([z][y][x]); v0 may be None (= 0)"""
+    u = _host_c(u0, N ** 3, "u0")
+    v = None if v0 is None else _host_c(v0, N ** 3, "v0")
+    _check(lib.kg_init_complex(N, L, dt, u.ctypes.data, None if v is None else v.ctypes.data), "kg_init_complex")
+    _state["N"] = N
+    _state["cplx"] = True
+
+
+def kg_init_complex_device(N, L, dt, d_u0, d_v0=None):
+    """device pointers (or complex128 torch tensors) of N^3 complex values each"""
+    _check(lib.kg_init_complex_device(N, L, dt, _dptr(d_u0), _dptr(d_v0)), "kg_init_complex_device")
+    _state["N"] = N
+    _state["cplx"] = True
+
+
+def kg_fetch_complex(N=None, out=None):
+    if out is None:
+        N = N or _state["N"]
+        out = np.empty((N, N, N), dtype=np.complex128)
+    _check(lib.kg_fetch_complex(out.ctypes.data), "kg_fetch_complex")
+    return out
+
+
+def kg_fetch_complex_device(d_u):
+    _check(lib.kg_fetch_complex_device(_dptr(d_u)), "kg_fetch_complex_device")
 
 
 def kg_step(n=1):
@@ -195,7 +236,7 @@ def kg_status():
 
 
 def kg_fetch_spectral(N):
-    a = np.empty((N, N, N // 2 + 1), dtype=np.complex128)
+    a = np.empty((N, N, N if _state.get("cplx") else N // 2 + 1), dtype=np.complex128)
     b = np.empty_like(a)
     _check(lib.kg_fetch_spectral(a.ctypes.data, b.ctypes.data), "kg_fetch_spectral")
     return a, b
@@ -226,7 +267,8 @@ class kg_state_header(C.Structure):
                 ("level", C.c_longlong), ("blowup_level", C.c_longlong), ("maxabs_last", C.c_double),
                 ("P_last", C.c_double), ("P_last_level", C.c_longlong), ("Q_last", C.c_double),
                 ("Q_last_level", C.c_longlong), ("have_E0", C.c_int), ("pad0", C.c_int), ("E0", C.c_double),
-                ("payload_bytes", C.c_ulonglong), ("checksum", C.c_ulonglong), ("reserved", C.c_ubyte * 96)]
+                ("payload_bytes", C.c_ulonglong), ("checksum", C.c_ulonglong), ("complex_field", C.c_int),
+                ("pad1", C.c_int), ("reserved", C.c_ubyte * 88)]
 
 
 STATE_HEADER_BYTES = 256
@@ -254,7 +296,9 @@ def kg_load_state(buf):
     if b.dtype != np.uint8:
         b = b.view(np.uint8)
     _check(lib.kg_load_state(b.ctypes.data, b.size), "kg_load_state")
-    _state["N"] = state_header(b).N
+    h = state_header(b)
+    _state["N"] = h.N
+    _state["cplx"] = bool(h.complex_field)
 
 
 def kg_state_checksum(payload):
