@@ -45,9 +45,10 @@ PAPER_TABLE1 = [("Hornet", 12288, 0.319), ("Juqueen", 262144, 0.350), ("Stampede
 # DRAM bytes (read + write) per launch of a step kernel at 512^3, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; the capture is summarised under
 # profiles/), valid only for the kernel sources it was taken on: KERNEL_SOURCES hashed
-TRAFFIC_512 = {}
-TRAFFIC_SOURCES_SHA = None
-KERNEL_SOURCES = ["kg_arith.cuh", "kg_fft.cuh", "kg_kernels.cuh", "kg_launch_impl.cuh"]
+TRAFFIC_512 = {("df64", "x"): 2095034112, ("df64", "yf"): 2096304896, ("df64", "zf"): 2096781312,
+               ("df64", "update"): 5338910720, ("df64", "zi"): 2096731392, ("df64", "yi"): 2096216832}
+TRAFFIC_SOURCES_SHA = "0c7d4d0c82d02f3d"
+KERNEL_SOURCES = ["kg_arith.cuh", "kg_fft.cuh", "kg_kernels.cuh", "kg_complex.cuh", "kg_launch_impl.cuh"]
 
 
 def kernel_sources_sha():
@@ -316,6 +317,8 @@ def main():
         if NG == 512:
             extras["paper_table1_protocol"] = {p: paper_protocol(kg, stream, torch, u0, NG, local, p)
                                                for p in ("df64", "fp64")}
+        extras["complex_field"] = {p: complex_point(kg, stream, torch, u0, NG, local, p, peak)
+                                   for p in ("df64", "mixed")}
     ens = None
     if not args.no_extras and rank == 0:
         ens = ensemble_point(kg, prec, args.ens_steps, torch, stream, early_exit=True)
@@ -346,6 +349,37 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def complex_point(kg, stream, torch, u0, NG, local, prec, peak):
+    """the complex-field path (|u|^2 u, full N^3 spectrum) on the same grid: u0 of the
+    workload times a phase exp(0.5 i x / L), steps/s and per-kernel device times; the
+    algorithmic bytes are those of the real path with S_c = N^3 16 B"""
+    x = (np.arange(NG) * (L_BOX / NG) - L_BOX / 2)
+    uc = (u0 * np.exp(0.5j * x / L_BOX)[None, None, :]).astype(np.complex128)
+    kg.kg_set_options(precision=prec, energy_every=ENERGY_EVERY)
+    d_u0 = torch.from_numpy(uc).to(f"cuda:{local}")
+    kg.kg_init_complex_device(NG, L_BOX, DT, d_u0, None)
+    del d_u0
+    kg.kg_step(ENERGY_EVERY)
+    stream.synchronize()
+    steps = 2 * ENERGY_EVERY
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps // ENERGY_EVERY):
+        kg.kg_step(ENERGY_EVERY)
+        kg.kg_energy(allow_drift=True)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    k_ms = [t / steps for t in kg.kg_step_timed(steps)]
+    sc = NG ** 3 * 16
+    w = sc if prec in ("fp64", "df64") else sc // 2
+    step_bytes = 8 * w + 3 * sc
+    kg.kg_finalize()
+    return {"steps_per_s": round(1e3 / ms, 2), "ms_per_step": round(ms, 4),
+            "kernel_ms": {n: round(t, 4) for n, t in zip(kg.STEP_KERNELS, k_ms)},
+            "step_hbm_frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4)}
 
 
 def paper_protocol(kg, stream, torch, u0, NG, local, prec):

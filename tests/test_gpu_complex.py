@@ -190,3 +190,22 @@ def test_wrong_kind_calls_are_refused(kg):
     bad[1, 2, 3] = complex(0, np.nan)
     assert kg.lib.kg_init_complex(N, L, 0.01, bad.ctypes.data, None) == kg.KG_EINVAL
     kg.kg_finalize()
+
+
+@pytest.mark.parametrize("prec", ["df64", "mixed"])
+def test_plane_wave_closed_form_512(kg, prec):
+    """the benchmark's grid size: the exact discrete plane wave after 60 steps"""
+    N, dt, A, m = 512, 0.005, 0.9, (5, -7, 3)
+    k2 = sum((2 * np.pi * mi / L) ** 2 for mi in m)
+    a = dt * dt * (1 + k2) / 4
+    c, beta = (1 - a) / (1 + a), (dt * dt / 2) / (1 + a)
+    th = math.acos(c + beta * A * A)
+    e = plane(N, m)
+    kg.kg_set_options(precision=prec)
+    kg.kg_init_complex(N, L, dt, A * e, -1j * A * math.sin(th) / dt * e)
+    kg.kg_step(60)
+    u = kg.kg_fetch_complex(N)
+    err = np.abs(u - A * np.exp(-60j * th) * e).max()
+    assert err <= (2e-12 if prec == "df64" else 2e-5) * A, (prec, err)
+    kg.kg_finalize()
+    kg.kg_set_options()
