@@ -31,6 +31,7 @@ L_BOX = 32.0
 DT = 0.005
 ENERGY_EVERY = 10
 PRECISION = "df64"
+STEP_LAUNCHES = 9
 METRIC = "512^3 KG steps/s"
 S_BYTES = N_GRID * N_GRID * (N_GRID // 2 + 1) * 16      # one complex128 half-spectrum array
 
@@ -340,7 +341,10 @@ def main():
                            "precision": prec, "energy_every": ENERGY_EVERY, "parallelism": "replicas",
                            "l2": "inputs larger than L2 (each state array 1.08 GB)"},
                 "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 6 * args.steps + 2 * (args.steps // ENERGY_EVERY),
+                # per step: x pass, its finaliser, two forward column passes, update, the
+                # second-stage Q sum, the z finaliser, two inverse column passes; per energy
+                # evaluation: the peek x pass and its finaliser
+                "gpu_launches": STEP_LAUNCHES * args.steps + 2 * (args.steps // ENERGY_EVERY),
                 "energy_series": {"every": ENERGY_EVERY, "first": energies[0] if energies else None,
                                   "max_rel_drift": (max(abs(e - energies[0]) for e in energies) / abs(energies[0])
                                                     if energies else None)},

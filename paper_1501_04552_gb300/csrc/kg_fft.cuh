@@ -125,13 +125,18 @@ __device__ __forceinline__ void dft8(cx<typename P::R>* u, int sg) {
     }
 }
 
-template <class P, int RADIX>
+// NORM: renormalise the outputs.  Between stages it is skipped: every output but the
+// first meets a twiddle product next, which renormalises, and an unnormalised pair
+// still represents its value to within u^2 times the sum of the magnitudes that formed it
+template <class P, int RADIX, bool NORM = true>
 __device__ __forceinline__ void dft(cx<typename P::R>* u, int sg) {
     if (RADIX == 8) dft8<P>(u, sg);
     else if (RADIX == 4) dft4<P>(u, sg);
     else if (RADIX == 2) dft2<P>(u);
+    if (NORM) {
 #pragma unroll
-    for (int r = 0; r < RADIX; r++) u[r] = P::cnorm(u[r]);
+        for (int r = 0; r < RADIX; r++) u[r] = P::cnorm(u[r]);
+    }
 }
 
 // Copy a twiddle table of n entries into shared memory once per CTA (all threads call
@@ -200,7 +205,7 @@ __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, cons
 #pragma unroll
             for (int r = 1; r < RADIX; r++) u[r] = P::ctw(u[r], twiddle<P>(tw, k * r * (n / (Ns * RADIX)) * twmul, sg));
         }
-        dft<P, RADIX>(u, sg);
+        dft<P, RADIX, LAST>(u, sg);
         if (LAST) {
 #pragma unroll
             for (int r = 0; r < RADIX; r++) out[q + r * Q] = u[r];
