@@ -137,3 +137,21 @@ def test_checkpoint_rejected_on_the_host(kg):
     assert kg.kg_get_options()["precision"] == kg.KG_MIXED
     assert kg.kg_get_options()["energy_every"] == 3
     kg.kg_set_options()
+
+
+def test_complex_entry_points_reject_bad_arguments_on_the_host(kg):
+    kg.lib.kg_finalize()
+    N = 16
+    u = np.zeros((N, N, N), dtype=np.complex128)
+    assert kg.lib.kg_init_complex(17, 32.0, 0.01, u.ctypes.data, None) == kg.KG_ENOTSUP
+    assert kg.lib.kg_init_complex(N, 32.0, -0.01, u.ctypes.data, None) == kg.KG_EINVAL
+    assert kg.lib.kg_init_complex(N, 32.0, 0.01, None, None) == kg.KG_EINVAL
+    bad = u.copy()
+    bad[2, 3, 4] = complex(np.inf, 0.0)
+    assert kg.lib.kg_init_complex(N, 32.0, 0.01, bad.ctypes.data, None) == kg.KG_EINVAL
+    v = u.copy()
+    v[0, 0, 1] = complex(0.0, np.nan)          # the imaginary parts are checked too
+    assert kg.lib.kg_init_complex(N, 32.0, 0.01, u.ctypes.data, v.ctypes.data) == kg.KG_EINVAL
+    out = np.empty((N, N, N), dtype=np.complex128)
+    assert kg.lib.kg_fetch_complex(out.ctypes.data) == kg.KG_ESTATE
+    assert kg.lib.kg_fetch_complex_device(None) == kg.KG_ESTATE
