@@ -320,6 +320,8 @@ def main():
                                                for p in ("df64", "fp64")}
         extras["complex_field"] = {p: complex_point(kg, stream, torch, u0, NG, local, p, peak)
                                    for p in ("df64", "mixed")}
+        if NG == 512:
+            extras["precision_split_500"] = precision_split(kg, torch, u0, NG, local, 500)
     ens = None
     if not args.no_extras and rank == 0:
         ens = ensemble_point(kg, prec, args.ens_steps, torch, stream, early_exit=True)
@@ -353,6 +355,32 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def precision_split(kg, torch, u0, NG, local, steps):
+    """the workload for `steps` steps in each precision, energy every 10: relative L2 of the
+    final field against the IEEE-FP64 path, and each path's energy drift (max |E - E_0| / |E_0|
+    over the series); the scheme's own O(dt^2) drift is in every path"""
+    out, fields = {}, {}
+    for prec in ("fp64", "df64", "mixed"):
+        kg.kg_set_options(precision=prec, energy_every=ENERGY_EVERY)
+        d_u0 = torch.from_numpy(u0).to(f"cuda:{local}")
+        kg.kg_init_device(NG, L_BOX, DT, d_u0, None)
+        del d_u0
+        es = [kg.kg_energy()]
+        for _ in range(steps // ENERGY_EVERY):
+            kg.kg_step(ENERGY_EVERY)
+            es.append(kg.kg_energy(allow_drift=True))
+        fields[prec] = kg.kg_fetch(NG)
+        es = np.array(es)
+        out[prec] = {"energy_drift": float(np.abs(es - es[0]).max() / abs(es[0]))}
+        kg.kg_finalize()
+    ref = fields["fp64"]
+    nrm = float(np.linalg.norm(ref))
+    for prec in ("df64", "mixed"):
+        out[prec]["rel_l2_vs_fp64"] = float(np.linalg.norm(fields[prec] - ref) / nrm)
+    out["steps"] = steps
+    return out
 
 
 def complex_point(kg, stream, torch, u0, NG, local, prec, peak):
