@@ -17,20 +17,7 @@ struct XcShape {
     static constexpr int PADN = N + N / 8;      // padded shared-memory slots per line
     static constexpr bool CTA_SYNC = T > 32;    // a line spans more than one warp
     static_assert(kXThreads % T == 0, "whole lines per CTA");
-};
-
-// one line's exchange space; a line wider than a warp synchronises the CTA (every
-// thread of the CTA runs the same transform, so the barrier is reached by all)
-template <class P, bool CTA>
-struct LineSmemX {
-    typename P::S* base;
-    static __device__ __forceinline__ int pad(int i) { return i + (i >> 3); }
-    __device__ __forceinline__ void put(int i, cx<typename P::R> v) { base[pad(i)] = P::pack(v); }
-    __device__ __forceinline__ cx<typename P::R> get(int i) const { return P::load(base[pad(i)]); }
-    __device__ __forceinline__ void sync() const {
-        if (CTA) __syncthreads();
-        else __syncwarp();
-    }
+    static_assert(!CTA_SYNC || LPC <= 15, "one named barrier per line");
 };
 
 // Pass X of a complex field.  MODE_STEP: per x-line, inverse transform, scale 1/N^3 ->
@@ -52,7 +39,7 @@ __global__ void __launch_bounds__(kXThreads, 2) k_pass_xc(typename P::S* __restr
 
     const int li = threadIdx.x / T, j = threadIdx.x % T;
     const size_t line = (size_t)blockIdx.x * X::LPC + li;
-    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN};
+    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN, 1u + (unsigned)li, (unsigned)T};
     const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev);
     const R rlam = P::from_f64(lam);
     S* __restrict__ L = W + line * N;
@@ -106,7 +93,7 @@ __global__ void __launch_bounds__(kXThreads) k_xc_forward(const double2* __restr
     double2* sm = reinterpret_cast<double2*>(smraw);
     const int li = threadIdx.x / T, j = threadIdx.x % T;
     const size_t line = (size_t)blockIdx.x * X::LPC + li;
-    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN};
+    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN, 1u + (unsigned)li, (unsigned)T};
     cx<double> v[8];
 #pragma unroll
     for (int s = 0; s < 8; s++) {
@@ -136,7 +123,7 @@ __global__ void __launch_bounds__(kXThreads) k_xc_inverse(const double2* __restr
     __shared__ double red[96];
     const int li = threadIdx.x / T, j = threadIdx.x % T;
     const size_t line = (size_t)blockIdx.x * X::LPC + li;
-    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN};
+    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN, 1u + (unsigned)li, (unsigned)T};
     cx<double> v[8];
 #pragma unroll
     for (int s = 0; s < 8; s++) {

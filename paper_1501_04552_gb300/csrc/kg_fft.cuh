@@ -177,6 +177,22 @@ struct LineSmem {
     __device__ __forceinline__ void sync() const { __syncwarp(); }
 };
 
+// one line's exchange space when a line may be wider than a warp (WIDE): such a line
+// synchronises its own warps on named barrier `bar` (1..15; nthreads of them), so the
+// lines of a CTA stay independent of one another
+template <class P, bool WIDE>
+struct LineSmemX {
+    typename P::S* base;
+    unsigned bar, nthreads;
+    static __device__ __forceinline__ int pad(int i) { return i + (i >> 3); }
+    __device__ __forceinline__ void put(int i, cx<typename P::R> v) { base[pad(i)] = P::pack(v); }
+    __device__ __forceinline__ cx<typename P::R> get(int i) const { return P::load(base[pad(i)]); }
+    __device__ __forceinline__ void sync() const {
+        if (WIDE) asm volatile("bar.sync %0, %1;\n" ::"r"(bar), "r"(nthreads) : "memory");
+        else __syncwarp();
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Stockham stage STAGE of a length-n transform.  Butterfly b (= j + T q) of a
 // radix-R stage with span Ns reads x[b + r n/R], applies exp(sg 2 pi i k r/(Ns R))

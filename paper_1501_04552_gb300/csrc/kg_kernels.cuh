@@ -101,6 +101,93 @@ __device__ __forceinline__ void x_line_body(const typename P::S* Lin, typename P
     }
 }
 
+// Two x-lines of a real field through one N-point complex transform.  Over the Hermitian
+// extensions of both half spectra (real parts only at kx = 0 and N/2, the C2R rule),
+// Z[k] = X1[k] + i X2[k] has the inverse transform u1 + i u2; after the cube, the forward
+// transform of F1 + i F2 splits again as
+//     X1[k] = (Z[k] + conj Z[N-k]) / 2,    X2[k] = -i (Z[k] - conj Z[N-k]) / 2,
+// which needs no twiddle product (the one-line form packs each line into an N/2-point
+// transform with a twiddle product per point on the way in and on the way out).
+template <int N>
+struct XpShape {
+    static constexpr int T = N / 8;              // threads per line pair
+    static constexpr int PPC = kXThreads / T;    // pairs per CTA
+    static constexpr int PADN = N + N / 8;       // padded exchange slots per pair
+    static constexpr bool CTA_SYNC = T > 32;     // a pair spans more than one warp
+    static_assert(2 * PPC == XShape<N>::LPC && PPC * PADN == XShape<N>::LPC * XShape<N>::PADM,
+                  "same lines and shared memory per CTA as the one-line form");
+    static_assert(!CTA_SYNC || PPC <= 15, "one named barrier per pair");
+};
+
+template <class P, int N, int MODE, class SM>
+__device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int j, SM& lsm,
+                                            const typename P::S* __restrict__ tw, double scale, typename P::R rlam,
+                                            bool want_sum, Stats<P>& st) {
+    typedef typename P::R R;
+    typedef cx<R> C;
+    constexpr int NH = N / 2 + 1, T = N / 8;
+    typename P::S* __restrict__ L2 = L1 + NH;
+    const R zero = P::from_f64(0.0);
+    C v[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        const int k = j + T * s;
+        const int kk = k <= N / 2 ? k : N - k;
+        C X1 = P::load(L1[kk]), X2 = P::load(L2[kk]);
+        if (kk == 0 || kk == N / 2) {      // real parts only
+            X1.im = zero;
+            X2.im = zero;
+        }
+        if (k > N / 2) {                    // Hermitian extension
+            X1 = conj(X1);
+            X2 = conj(X2);
+        }
+        v[s] = P::cnorm(cmake<R>(P::rsub(X1.re, X2.im), P::radd(X1.im, X2.re)));   // X1 + i X2
+    }
+#pragma unroll 1
+    for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
+        fft<P, N>(v, j, tw, 1, lsm, dir == 0 ? +1 : -1);
+        if (dir == 0) {
+#pragma unroll
+            for (int s = 0; s < 8; s++) {
+                v[s].re = P::scale2(v[s].re, scale);   // u1, u2 at x = j + T s; scale = 1/N^3
+                v[s].im = P::scale2(v[s].im, scale);
+                st.take(v[s].re, want_sum);
+                st.take(v[s].im, want_sum);
+            }
+            if (MODE == MODE_STEP) {
+#pragma unroll
+                for (int s = 0; s < 8; s++) {
+                    v[s].re = rlam * (v[s].re * v[s].re * v[s].re);
+                    v[s].im = rlam * (v[s].im * v[s].im * v[s].im);
+                }
+            }
+        }
+    }
+    if (MODE == MODE_STEP) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) lsm.put(j + T * s, v[s]);
+        lsm.sync();
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            const int k = j + T * s;
+            if (k <= N / 2) {
+                const C Z = v[s];
+                const C Zm = conj(lsm.get((N - k) & (N - 1)));
+                const C A = P::cadd(Z, Zm), B = P::csub(Z, Zm);      // 2 X1, 2 i X2
+                C x1 = P::cnorm(A), x2 = P::cnorm(cmake<R>(B.im, -B.re));
+                x1.re = P::scale2(x1.re, 0.5);
+                x1.im = P::scale2(x1.im, 0.5);
+                x2.re = P::scale2(x2.re, 0.5);
+                x2.im = P::scale2(x2.im, 0.5);
+                L1[k] = P::pack(x1);
+                L2[k] = P::pack(x2);
+            }
+        }
+        lsm.sync();
+    }
+}
+
 // one element global -> shared without registers (8- or 16-byte values)
 template <class S>
 __device__ __forceinline__ void cp_async_elem(S* smem, const S* gmem) {
@@ -112,6 +199,17 @@ __device__ __forceinline__ void cp_async_elem(S* smem, const S* gmem) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
     }
 }
+
+// The double-float pass takes x-lines in pairs (x_pair_body): fewer FP32 operations
+// per point, which is what bounds it.
+template <class P>
+struct XPaired {
+    static constexpr bool value = false;
+};
+template <>
+struct XPaired<PrecDF> {
+    static constexpr bool value = true;
+};
 
 // How pass X walks W.  Pipelined (FP32 and FP64 passes, bound by latency and by the
 // FP64 pipe): a persistent grid walks the batches, and while a CTA transforms one batch
@@ -151,7 +249,13 @@ __global__ void __launch_bounds__(kXThreads, 2) k_pass_x(typename P::S* __restri
     Stats<P> st;
     st.init();
 
-    if constexpr (!XPipelined<P>::value) {
+    if constexpr (!XPipelined<P>::value && XPaired<P>::value) {
+        typedef XpShape<N> XP;
+        const int pi = threadIdx.x / XP::T, jp = threadIdx.x % XP::T;
+        const size_t pair = (size_t)blockIdx.x * XP::PPC + pi;
+        LineSmemX<P, XP::CTA_SYNC> lsm{buf + pi * XP::PADN, 1u + (unsigned)pi, (unsigned)XP::T};
+        x_pair_body<P, N, MODE>(W + 2 * pair * NH, jp, lsm, tw, scale, rlam, want_sum, st);
+    } else if constexpr (!XPipelined<P>::value) {
         const size_t line = (size_t)blockIdx.x * LPC + li;
         LineSmem<P> lsm{buf + li * PADM};
         x_line_body<P, N, MODE>(W + line * NH, W + line * NH, j, lsm, tw, scale, rlam, want_sum, st);
