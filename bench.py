@@ -3,8 +3,8 @@
 Workload (the paper-scale case): N = 512 (R2C storage 512 x 512 x 257 complex128),
 cube side 32, u0 = 0.1 exp(-|x|^2) + 1e-3 lowpass(N(0,1), |m| <= 8) seeded 1501,
 u_t(0) = 0, dt = 0.005, energy every 10 steps.  A "step" is one pass of the whole
-hot path: x pass (C2R, cube, R2C), forward y pass, z pass with the FP64 update, and
-inverse y pass, plus the recorded energy sums every 10th level.
+hot path: x pass (C2R, cube, R2C), forward y and z passes, the FP64 update, inverse z
+and y passes, plus the recorded energy sums every 10th level.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 

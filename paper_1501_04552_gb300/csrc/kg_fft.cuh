@@ -1,16 +1,19 @@
-// kg_fft.cuh -- shared-memory Stockham FFTs and the fused passes of one time step.
+// kg_fft.cuh -- shared-memory Stockham FFTs and the pieces the passes of a step share.
 //
 // One time step of the scheme of section 1.1.2 (Eq. (2), stepped in Fourier space
-// with the cube formed in real space, two 3D FFTs per step) is four passes over the
-// work array W (half spectrum in x, [z][y][kx] / [kz][ky][kx], kx = 0..N/2 fastest):
+// with the cube formed in real space, two 3D FFTs per step) is a sequence of passes
+// over the work array W (half spectrum in x, [z][y][kx] / [kz][ky][kx], kx = 0..N/2
+// fastest):
 //
-//   X  : per x-line, complex-to-real inverse along x (N-point real transform through
-//        an N/2-point complex FFT), scale 1/N^3 -> u^n on the line; max|u|, sum u^4;
-//        F = lam u^3; real-to-complex forward along x; written back in place.
+//   X  : per x-line, complex-to-real inverse along x, scale 1/N^3 -> u^n on the line;
+//        max|u|, sum u^4; F = lam u^3; real-to-complex forward along x; in place.
+//        (One line through an N/2-point complex FFT, or two lines through one N-point
+//        complex FFT.)
 //   Yf : per (z, kx) column, forward complex FFT along y, in place.
-//   Z  : per (ky, kx) column, forward complex FFT along z -> F^n_k; the FP64 update
-//        uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k written over uh^{n-1};
-//        optional Q^{n+1/2} partial sums; inverse complex FFT along z of uh^{n+1} -> W.
+//   Zf : per (ky, kx) column, forward complex FFT along z -> F^n_k, in place.
+//   U  : per mode, the FP64 update uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k
+//        written over uh^{n-1} and into W; optional Q^{n+1/2} partial sums.
+//   Zi : per (ky, kx) column, inverse complex FFT along z, in place.
 //   Yi : per (z, kx) column, inverse complex FFT along y, in place.
 //
 // The pencil transposes of a distributed 3D FFT become strided column accesses:

@@ -364,7 +364,9 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col_sel(const double
 }
 
 // ---------------------------------------------------------------------------
-// Pass Z: forward z FFT -> F^n, FP64 update, optional Q terms, inverse z FFT.
+// Fused z column: forward z FFT -> F^n, FP64 update, optional Q terms, inverse z FFT,
+// in one pass over W (the batched ensemble's z pass; the single-state step runs the
+// three parts as separate kernels, which measured faster at 512^3).
 // coef[m2] = (2 c_k, 2 beta_k) for integer m2 = mx^2 + my^2 + mz^2; w2[m2] = omega_k^2.
 // ---------------------------------------------------------------------------
 // one (ky, kx) column (T = N/8 threads, thread j); update == false leaves the state
@@ -444,10 +446,9 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
 }
 
 // ---------------------------------------------------------------------------
-// Streaming update (the z pass split in three: forward z FFT, this kernel, inverse z
-// FFT).  W holds F^n_k on entry and uh^{n+1}_k in the pass precision on exit; the state
-// update and the Q terms are those of z_body.  Each thread takes kUpdItems consecutive
-// modes per round and issues all their loads before any arithmetic.
+// Streaming update between the forward and the inverse z FFT.  W holds F^n_k on entry
+// and uh^{n+1}_k in the pass precision on exit; the state update and the Q terms are
+// those of z_body.
 // ---------------------------------------------------------------------------
 // The mode stored at index i of a spectral array: the half spectrum of a real field
 // ([kz][ky][kx], kx = 0..N/2) or the full spectrum of a complex field (kx = 0..N-1 in
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(kFinThreads) k_fin_peek(const double* part_sum
     }
 }
 
-// after the z pass: Q^{l+1/2} (q_norm = h^3/N^3) and the level advance
+// after the update: Q^{l+1/2} (q_norm = h^3/N^3) and the level advance
 __global__ void __launch_bounds__(kSumThreads) k_sum_parts(const double* __restrict__ in, int count,
                                                            double* __restrict__ out, const KgDev* __restrict__ dev) {
     if (!kg_recording(dev)) return;
