@@ -134,9 +134,9 @@ __device__ __forceinline__ void ens_unit(const EnsParams& p, int ii, int unit, i
         const bool valid = tile_ok && kx < NH;
         ColSmem<P, C> csm{sm + sub * (N * C), c};
         if (pass == 1) {
-            col_body<P, P, P, N, -1>(W, W, (size_t)plane * N * NH + kx, NH, valid, j, csm, tw);
+            col_body<P, P, P, N, -1, C>(W, W, (size_t)plane * N * NH + kx, NH, valid, j, csm, tw);
         } else if (pass == 3) {
-            col_body<P, P, P, N, +1>(W, W, (size_t)plane * N * NH + kx, NH, valid, j, csm, tw);
+            col_body<P, P, P, N, +1, C>(W, W, (size_t)plane * N * NH + kx, NH, valid, j, csm, tw);
         } else {
             double2* cur = inst_phase ? in.S1 : in.S0;
             double2* old = inst_phase ? in.S0 : in.S1;

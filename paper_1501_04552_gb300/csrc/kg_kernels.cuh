@@ -308,12 +308,21 @@ template <class P>
 struct ColShape {
     static constexpr int C = 128 / (int)sizeof(typename P::S);
 };
+// Column tiles of the single-state step: 128-byte rows, except the FP32 y passes, whose
+// rows are N/2+1 values apart (the z rows are a whole plane apart): there 64-byte rows
+// gave twice the CTAs for the same occupancy and measured faster (0.227 against
+// 0.244 ms at 512^3), while every z pass and the 16-byte y passes were as fast or faster
+// with 128 bytes.
+template <class P, bool YPASS>
+struct ColStep {
+    static constexpr int C = (YPASS && sizeof(typename P::S) == 8 ? 64 : 128) / (int)sizeof(typename P::S);
+};
 
 // one column (T = N/8 threads, thread j) of a tile; valid == false for the columns
 // of the last tile beyond kx = N/2 (they compute on zeros and store nothing)
-template <class Pin, class P, class Pout, int N, int SIGN>
+template <class Pin, class P, class Pout, int N, int SIGN, int CW>
 __device__ __forceinline__ void col_body(const typename Pin::S* src, typename Pout::S* dst, size_t base,
-                                         size_t row_stride, bool valid, int j, ColSmem<P, ColShape<P>::C>& csm,
+                                         size_t row_stride, bool valid, int j, ColSmem<P, CW>& csm,
                                          const typename P::S* __restrict__ tw) {
     typedef typename P::R R;
     constexpr int T = N / 8;
@@ -331,28 +340,28 @@ __device__ __forceinline__ void col_body(const typename Pin::S* src, typename Po
 }
 
 // NC columns per plane: N/2 + 1 (half spectrum of a real field) or N (complex field)
-template <class Pin, class P, class Pout, int N, int SIGN, int NC = N / 2 + 1>
-__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col(const typename Pin::S* src, typename Pout::S* dst,
+template <class Pin, class P, class Pout, int N, int SIGN, int NC = N / 2 + 1, int CW = ColShape<P>::C>
+__global__ void __launch_bounds__(CW * N / 8) k_col(const typename Pin::S* src, typename Pout::S* dst,
                                                                size_t plane_stride, size_t row_stride,
                                                                const typename P::S* __restrict__ tw) {
-    constexpr int C = ColShape<P>::C;
+    constexpr int C = CW;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
     const int c = threadIdx.x % C, j = threadIdx.x / C;
     const int kx = blockIdx.x * C + c;
     ColSmem<P, C> csm{sm, c};
     tw = stage_table(tw, sm + N * C, N);
-    col_body<Pin, P, Pout, N, SIGN>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NC, j, csm, tw);
+    col_body<Pin, P, Pout, N, SIGN, C>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NC, j, csm, tw);
 }
 
 // inverse column FFT from an FP64 spectral array into W (precision P); the source is
 // src1 when dev != NULL and dev->phase == 1, src0 otherwise (the current level's array)
-template <class P, int N, int NC = N / 2 + 1>
-__global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col_sel(const double2* src0, const double2* src1,
+template <class P, int N, int NC = N / 2 + 1, int CW = ColShape<P>::C>
+__global__ void __launch_bounds__(CW * N / 8) k_col_sel(const double2* src0, const double2* src1,
                                                                    const KgDev* dev, typename P::S* dst,
                                                                    size_t plane_stride, size_t row_stride,
                                                                    const typename P::S* __restrict__ tw) {
-    constexpr int C = ColShape<P>::C;
+    constexpr int C = CW;
     extern __shared__ __align__(16) unsigned char smraw[];
     typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
     const double2* src = (dev != nullptr && dev->phase) ? src1 : src0;
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(ColShape<P>::C * N / 8) k_col_sel(const double
     const int kx = blockIdx.x * C + c;
     ColSmem<P, C> csm{sm, c};
     tw = stage_table(tw, sm + N * C, N);
-    col_body<PrecF64, P, P, N, +1>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NC, j, csm, tw);
+    col_body<PrecF64, P, P, N, +1, C>(src, dst, (size_t)blockIdx.y * plane_stride + kx, row_stride, kx < NC, j, csm, tw);
 }
 
 // ---------------------------------------------------------------------------

@@ -86,21 +86,29 @@ struct Launchers {
         KG_DISPATCH_N(N, return x_grid_n<NN>());
     }
 
-    template <int N, int SIGN, int NC = N / 2 + 1>
+    template <int N, int SIGN, int NC = N / 2 + 1, int C = ColShape<P>::C>
     static cudaError_t col_n(void* W, size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
-        constexpr int C = ColShape<P>::C;
         const size_t smem = (size_t)(N * C + N) * sizeof(S);
-        auto kern = k_col<P, P, P, N, SIGN, NC>;
+        auto kern = k_col<P, P, P, N, SIGN, NC, C>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
         dim3 grid((NC + C - 1) / C, nplanes);
         kern<<<grid, C * N / 8, smem, st>>>((const S*)W, (S*)W, pstride, rstride, (const S*)tw);
         return cudaGetLastError();
     }
+    // y passes (row stride of one x-row) and z passes (row stride of a plane) take the
+    // tile widths of ColStep
+    template <int N, int SIGN, int NC>
+    static cudaError_t col_yz(void* W, size_t pstride, size_t rstride, int nplanes, const void* tw,
+                              cudaStream_t st) {
+        if (rstride <= (size_t)N)
+            return col_n<N, SIGN, NC, ColStep<P, true>::C>(W, pstride, rstride, nplanes, tw, st);
+        return col_n<N, SIGN, NC, ColStep<P, false>::C>(W, pstride, rstride, nplanes, tw, st);
+    }
     static cudaError_t col(int N, int sign, void* W, size_t pstride, size_t rstride, int nplanes, const void* tw,
                            cudaStream_t st) {
-        if (sign < 0) { KG_DISPATCH_N(N, return (col_n<NN, -1>(W, pstride, rstride, nplanes, tw, st))); }
-        KG_DISPATCH_N(N, return (col_n<NN, +1>(W, pstride, rstride, nplanes, tw, st)));
+        if (sign < 0) { KG_DISPATCH_N(N, return (col_yz<NN, -1, NN / 2 + 1>(W, pstride, rstride, nplanes, tw, st))); }
+        KG_DISPATCH_N(N, return (col_yz<NN, +1, NN / 2 + 1>(W, pstride, rstride, nplanes, tw, st)));
     }
 
     template <int N, int NC = N / 2 + 1>
@@ -108,7 +116,7 @@ struct Launchers {
                                       size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
         constexpr int C = ColShape<P>::C;
         const size_t smem = (size_t)(N * C + N) * sizeof(S);
-        auto kern = k_col_sel<P, N, NC>;
+        auto kern = k_col_sel<P, N, NC, C>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
         dim3 grid((NC + C - 1) / C, nplanes);
@@ -157,8 +165,8 @@ struct Launchers {
     static int xc_parts(int N) { return N * N / (kXThreads / (N / 8)); }
     static cudaError_t colc(int N, int sign, void* W, size_t pstride, size_t rstride, int nplanes, const void* tw,
                             cudaStream_t st) {
-        if (sign < 0) { KG_DISPATCH_N(N, return (col_n<NN, -1, NN>(W, pstride, rstride, nplanes, tw, st))); }
-        KG_DISPATCH_N(N, return (col_n<NN, +1, NN>(W, pstride, rstride, nplanes, tw, st)));
+        if (sign < 0) { KG_DISPATCH_N(N, return (col_yz<NN, -1, NN>(W, pstride, rstride, nplanes, tw, st))); }
+        KG_DISPATCH_N(N, return (col_yz<NN, +1, NN>(W, pstride, rstride, nplanes, tw, st)));
     }
     static cudaError_t colc_from_f64(int N, const double2* src0, const double2* src1, const KgDev* dev, void* W,
                                      size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
