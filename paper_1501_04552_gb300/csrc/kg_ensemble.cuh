@@ -111,14 +111,25 @@ __device__ __forceinline__ void ens_unit(const EnsParams& p, int ii, int unit, i
     const S* tw = (const S*)tb.tw;
     S* W = (S*)in.W;
     if (pass == 0) {
-        constexpr int T = N / 16;
-        const int li = threadIdx.x / T, j = threadIdx.x % T;
-        const size_t line = (size_t)unit * U::LPU + li;
-        LineSmem<P> lsm{sm + li * XShape<N>::PADM};
         Stats<P> st;
         st.init();
-        x_line_body<P, N, MODE_STEP>(W + line * NH, W + line * NH, j, lsm, tw, 1.0 / ((double)N * N * N), P::from_f64(p.lam),
-                                     false, st);
+        if constexpr (XPaired<P>::value) {
+            // lines in pairs through one N-point transform (a pair fits in one warp here)
+            typedef XpShape<N> XP;
+            static_assert(!XP::CTA_SYNC, "ensemble grids keep a line pair inside a warp");
+            const int pi = threadIdx.x / XP::T, jp = threadIdx.x % XP::T;
+            const size_t pair = (size_t)unit * (U::LPU / 2) + pi;
+            LineSmemX<P, false> lsm{sm + pi * XP::PADN, 0u, 0u};
+            x_pair_body<P, N, MODE_STEP>(W + 2 * pair * NH, jp, lsm, tw, 1.0 / ((double)N * N * N),
+                                         P::from_f64(p.lam), false, st);
+        } else {
+            constexpr int T = N / 16;
+            const int li = threadIdx.x / T, j = threadIdx.x % T;
+            const size_t line = (size_t)unit * U::LPU + li;
+            LineSmem<P> lsm{sm + li * XShape<N>::PADM};
+            x_line_body<P, N, MODE_STEP>(W + line * NH, W + line * NH, j, lsm, tw, 1.0 / ((double)N * N * N),
+                                         P::from_f64(p.lam), false, st);
+        }
         const unsigned k2 = st.fkey();
         const unsigned wmax = __reduce_max_sync(0xffffffffu, k2);
         if ((threadIdx.x & 31) == 0) atomicMax(maxkey_row + ii, wmax);
