@@ -77,6 +77,28 @@ def algorithmic_bytes(prec, n=N_GRID):
     return per_kernel, 8 * w + 3 * s_bytes
 
 
+# FP32 issue peak of the GPU: 152 SMs x 128 FP32 lanes x 2.07 GHz (max SM clock), one
+# instruction per lane per clock
+FP32_ISSUE_PEAK = 152 * 128 * 2.07e9
+
+
+def df64_fp32_ops(n):
+    """FP32 operations of the double-float FFT kernels at grid n, counted from the
+    definitions of the double-float arithmetic (Knuth two-sum 6 + low parts 2 = 8 per
+    unnormalised add, 19 per FMA-split dot product = one component of a twiddle product,
+    3 per renormalisation, 7 per double-float product; sign flips and integer work not
+    counted).  Radix-8 DFT without renormalisation: 24 complex adds (384) + the two
+    sqrt(1/2) rotations (60) = 444; the last stage renormalises its 8 outputs (+48); a
+    stage after the first applies 7 twiddle products (+266).  Returns per-launch counts
+    for the paired x pass and for one column pass (n = 512: three radix-8 stages)."""
+    assert n == 512
+    fft_point = (444 + (444 + 266) + (444 + 266 + 48)) / 8.0      # 239 per point
+    pairs = n * n // 2
+    per_pair = n * (22 + fft_point + 4 + 42 + fft_point) + (n // 2 + 1) * 52
+    col_points = n * n * (n // 2 + 1)
+    return {"x": pairs * per_pair, "col": col_points * fft_point}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -283,8 +305,20 @@ def main():
                 "step_achieved": round(step_achieved, 1), "step_frac": round(step_achieved / peak, 4),
                 "kernels": per_kernel}
     if prec == "df64":
-        roofline["limiter"] = ("double-float FFT kernels are FP32-issue-bound (x pass: issue active ~72 % in "
-                               "ncu); their HBM fraction is low by construction")
+        roofline["limiter"] = ("double-float FFT kernels are FP32-issue-bound (ncu: issue active 76-78 %); "
+                               "their HBM fraction is low by construction, see roofline_alu")
+    roofline_alu = None
+    if prec == "df64" and NG == 512:
+        ops = df64_fp32_ops(NG)
+        per = {n: {"ops": ops["x" if n == "x" else "col"],
+                   "frac": round(ops["x" if n == "x" else "col"] / (t * 1e-3) / FP32_ISSUE_PEAK, 4)}
+               for n, t in zip(names, k_avg) if n != "update"}
+        x_rate = ops["x"] / (k_avg[names.index("x")] * 1e-3)
+        roofline_alu = {"bound": "alu", "kernel": "k_pass_x", "achieved": round(x_rate / 1e12, 2),
+                        "peak": round(FP32_ISSUE_PEAK / 1e12, 2), "unit": "T FP32 ops/s",
+                        "frac": round(x_rate / FP32_ISSUE_PEAK, 4), "kernels": per,
+                        "what": "double-float operation counts of the FFT kernels / event time; "
+                                "peak = 152 SMs x 128 lanes x 2.07 GHz"}
 
     # end to end through the public API with host buffers: pinned u0 -> kg_init, K steps, kg_fetch -> host
     pinned_u0 = torch.from_numpy(u0).pin_memory()
@@ -342,7 +376,8 @@ def main():
                 "config": {"workload": "kg%d_bump_noise" % NG, "N": NG, "L": L_BOX, "dt": DT, "seed": 1501,
                            "precision": prec, "energy_every": ENERGY_EVERY, "parallelism": "replicas",
                            "l2": "inputs larger than L2 (each state array 1.08 GB)"},
-                "roofline": roofline, "cpu_baseline": base, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "roofline_alu": roofline_alu, "cpu_baseline": base, "e2e": e2e,
+                "clocks": clocks,
                 # per step: x pass, its finaliser, two forward column passes, update, the
                 # second-stage Q sum, the z finaliser, two inverse column passes; per energy
                 # evaluation: the peek x pass and its finaliser

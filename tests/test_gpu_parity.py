@@ -258,3 +258,59 @@ def test_drift_watchdog(kg):
     assert ei.value.code == kg.KG_EDRIFT
     assert math.isfinite(kg.kg_energy(allow_drift=True))
     kg.kg_set_options()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_degenerate_inputs(kg, oracle, prec):
+    """the zero field stays exactly zero with zero energy; a start from rest position with
+    a velocity only (u0 = 0) follows the oracle; kg_step(0) changes nothing"""
+    N, dt = 32, 0.02
+    z = np.zeros((N, N, N))
+    kg.kg_set_options(precision=prec, energy_every=2)
+    kg.kg_init(N, L, dt, z, None)
+    kg.kg_step(6)
+    assert not np.any(kg.kg_fetch(N)) and kg.kg_energy() == 0.0
+    v0 = 0.3 * I.gaussian(N, L, 1.0, 2.5) * I.plane_wave(N, L, (1, 0, 2), "cos")
+    kg.kg_init(N, L, dt, z, v0)
+    ref = oracle.Solver(N, L, dt, z, v0)
+    kg.kg_step(9)
+    ref.step(9)
+    u = kg.kg_fetch(N)
+    assert rel(u, ref.fetch()) <= TOL[prec]
+    a0, b0 = kg.kg_fetch_spectral(N)
+    kg.kg_step(0)
+    a1, b1 = kg.kg_fetch_spectral(N)
+    assert np.array_equal(a0, a1) and np.array_equal(b0, b1) and kg.kg_status()["level"] == 9
+    kg.kg_set_options()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_max_abs_matches_oracle(kg, oracle, prec):
+    """max|u| of the last stepped level, read from integer keys: FP64 bit patterns for the
+    FP64 passes, FP32 bit patterns otherwise"""
+    N, dt = 32, 0.02
+    u0, v0 = smooth_ic(N, 4)
+    kg.kg_set_options(precision=prec)
+    kg.kg_init(N, L, dt, u0, v0)
+    kg.kg_step(7)
+    ref = oracle.Solver(N, L, dt, u0, v0)
+    ref.step(7)
+    tol = {"fp64": 1e-12, "df64": 2.0 ** -23, "mixed": 1e-5}[prec]
+    assert abs(kg.kg_status()["maxabs"] - ref.last_maxabs) <= tol * ref.last_maxabs
+    kg.kg_set_options()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_linear_mode_large_dt(kg, prec):
+    """the linear part is unconditionally stable: dt = 0.9 still follows the discrete dispersion"""
+    N, dt, m, b, n = 32, 0.9, (2, -1, 3), 0.3, 40
+    u0 = I.plane_wave(N, L, m, "cos")
+    v0 = b * I.plane_wave(N, L, m, "sin")
+    kg.kg_set_options(precision=prec, nonlinearity=0.0)
+    kg.kg_init(N, L, dt, u0, v0)
+    kg.kg_step(n)
+    k2 = sum((2 * np.pi * mi / L) ** 2 for mi in m)
+    th = 2 * math.atan(dt * math.sqrt(1 + k2) / 2)
+    ref = math.cos(n * th) * u0 + dt * b * math.sin(n * th) / math.sin(th) * I.plane_wave(N, L, m, "sin")
+    assert np.abs(kg.kg_fetch(N) - ref).max() <= (1e-12 if prec != "mixed" else 1e-5)
+    kg.kg_set_options()
