@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/kg.h"
@@ -149,9 +150,37 @@ int inverse_yz_f64(Ctx* c, const double2* src0, const double2* src1, const KgDev
 
 double inv_n3(int N) { return 1.0 / ((double)N * (double)N * (double)N); }
 
+// 1 if a[0..n) holds an infinity or a NaN: exponent field all ones, tested on the bit
+// patterns without branches so the loop vectorises
+int nonfinite_in(const double* a, size_t n) {
+    unsigned long long bad = 0;
+    for (size_t i = 0; i < n; i++) {
+        unsigned long long b;
+        std::memcpy(&b, a + i, 8);
+        bad |= (unsigned long long)((b & 0x7FF0000000000000ull) == 0x7FF0000000000000ull);
+    }
+    return bad != 0;
+}
+
+// host-side check of an input field; large fields are split across host threads
 int check_finite(const double* a, size_t n, const char* what) {
-    for (size_t i = 0; i < n; i++)
-        if (!std::isfinite(a[i])) return fail(KG_EINVAL, std::string(what) + " has a non-finite entry");
+    const size_t kChunk = (size_t)1 << 22;
+    int bad = 0;
+    if (n <= kChunk) {
+        bad = nonfinite_in(a, n);
+    } else {
+        const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        const size_t per = (n + hw - 1) / hw;
+        std::vector<int> flags(hw, 0);
+        std::vector<std::thread> pool;
+        for (unsigned t = 0; t < hw; t++) {
+            const size_t lo = std::min(n, (size_t)t * per), hi = std::min(n, lo + per);
+            pool.emplace_back([a, lo, hi, t, &flags] { flags[t] = nonfinite_in(a + lo, hi - lo); });
+        }
+        for (auto& th : pool) th.join();
+        for (int f : flags) bad |= f;
+    }
+    if (bad) return fail(KG_EINVAL, std::string(what) + " has a non-finite entry");
     return KG_OK;
 }
 
@@ -163,9 +192,61 @@ int check_grid(int N, double L, double dt) {
     return KG_OK;
 }
 
+// release one allocation of a context (the small per-grid tables on reuse)
+void release(Ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
+        if (*it == p) {
+            c->allocs.erase(it);
+            cudaFree(p);
+            c->bytes -= bytes;
+            return;
+        }
+}
+
+// A new run on the grid, precision and field kind of the current context keeps its
+// device buffers (several GB at 512^3, whose release and allocation cost more than the
+// set-up itself); only the tables, which depend on L and dt, and the captured step
+// graph, whose launch parameters depend on them, are rebuilt.
+int reuse_ctx(Ctx* c, double L, double dt, Ctx** out) {
+    cudaStream_t st = stream_of(c);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(KG_ECUDA, "reuse: stream sync");
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    c->step_graph = nullptr;
+    c->launched = 0;
+    const int N = c->N;
+    const int m2max = 3 * (N / 2) * (N / 2);
+    if (c->tw != (void*)c->tw64) release(c, c->tw, c->pl->store_bytes * N);
+    release(c, c->tw64, sizeof(double2) * N);
+    release(c, c->coef, sizeof(double2) * (m2max + 1));
+    release(c, c->w2, sizeof(double) * (m2max + 1));
+    c->tw = c->tw64 = nullptr;
+    c->coef = nullptr;
+    c->w2 = nullptr;
+    c->L = L;
+    c->dt = dt;
+    c->lam = g_opt.nonlinearity;
+    c->have_E0 = false;
+    c->E0 = 0.0;
+    int rc = upload_tables(c);
+    if (rc) {
+        destroy(c);
+        return rc;
+    }
+    *out = c;
+    return KG_OK;
+}
+
 // a context for an N^3 run in the current options, with every buffer a step needs;
-// replaces (destroys) the previous context first.  On failure nothing is kept.
+// replaces the previous context (reusing its buffers when the shapes match).  On
+// failure nothing is kept.
 int create_ctx(int N, double L, double dt, bool cplx, Ctx** out) {
+    if (g_ctx && g_ctx->N == N && g_ctx->cplx == cplx && g_ctx->prec == g_opt.precision &&
+        !std::getenv("KG_TEST_FAIL_ALLOC")) {
+        Ctx* c = g_ctx;
+        g_ctx = nullptr;
+        return reuse_ctx(c, L, dt, out);
+    }
     if (g_ctx) {
         destroy(g_ctx);
         g_ctx = nullptr;

@@ -155,3 +155,16 @@ def test_complex_entry_points_reject_bad_arguments_on_the_host(kg):
     out = np.empty((N, N, N), dtype=np.complex128)
     assert kg.lib.kg_fetch_complex(out.ctypes.data) == kg.KG_ESTATE
     assert kg.lib.kg_fetch_complex_device(None) == kg.KG_ESTATE
+
+
+def test_large_field_finiteness_check_on_the_host(kg):
+    """fields above 4M values are checked by several host threads: a bad value in any
+    chunk, the last one included, is still found before anything touches the GPU"""
+    N = 256
+    u = np.zeros((N, N, N))
+    for pos in [(0, 0, 0), (128, 7, 3), (N - 1, N - 1, N - 1)]:
+        u[pos] = np.nan
+        assert kg.lib.kg_init(N, 32.0, 0.01, u.ctypes.data, None) == kg.KG_EINVAL
+        u[pos] = -np.inf
+        assert kg.lib.kg_init(N, 32.0, 0.01, u.ctypes.data, None) == kg.KG_EINVAL
+        u[pos] = 0.0
