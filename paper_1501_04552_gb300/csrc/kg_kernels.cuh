@@ -211,6 +211,17 @@ struct XPaired<PrecDF> {
     static constexpr bool value = true;
 };
 
+// resident CTAs per SM the x pass is compiled for: the paired double-float body fits
+// three (80 registers, no spills); the FP32 and FP64 bodies need more registers
+template <class P>
+struct XMinBlocks {
+    static constexpr int value = 2;
+};
+template <>
+struct XMinBlocks<PrecDF> {
+    static constexpr int value = 3;
+};
+
 // How pass X walks W.  Pipelined (FP32 and FP64 passes, bound by latency and by the
 // FP64 pipe): a persistent grid walks the batches, and while a CTA transforms one batch
 // from shared memory the next one lands in the other half of a double buffer
@@ -230,7 +241,7 @@ struct XPipelined<PrecDF> {
 // of W; a landed batch serves as the lines' FFT exchange space.  Each CTA writes one
 // max key and (when wanted) one Sigma u^4 partial.
 template <class P, int N, int MODE>
-__global__ void __launch_bounds__(kXThreads, 2) k_pass_x(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
+__global__ void __launch_bounds__(kXThreads, XMinBlocks<P>::value) k_pass_x(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
                                                       double* __restrict__ part_sum, double* __restrict__ part_max,
                                                       const typename P::S* __restrict__ tw, double scale, double lam) {
     typedef typename P::S S;
