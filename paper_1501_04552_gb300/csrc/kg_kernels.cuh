@@ -219,7 +219,7 @@ struct XMinBlocks {
 };
 template <>
 struct XMinBlocks<PrecDF> {
-    static constexpr int value = 3;
+    static constexpr int value = 4;
 };
 
 // How pass X walks W.  Pipelined (FP32 and FP64 passes, bound by latency and by the
