@@ -20,11 +20,22 @@ struct XcShape {
     static_assert(!CTA_SYNC || LPC <= 15, "one named barrier per line");
 };
 
+// resident CTAs per SM the complex x pass is compiled for (the largest count whose
+// register budget needs no spills, FP64 excepted)
+template <class P>
+struct XcMinBlocks {
+    static constexpr int value = 4;
+};
+template <>
+struct XcMinBlocks<PrecF64> {
+    static constexpr int value = 2;
+};
+
 // Pass X of a complex field.  MODE_STEP: per x-line, inverse transform, scale 1/N^3 ->
 // u^n; |u|^2 keys and (when wanted) sum |u|^4; F = lam |u|^2 u; forward transform;
 // written back in place.  MODE_PEEK: inverse transform and the statistics only.
 template <class P, int N, int MODE>
-__global__ void __launch_bounds__(kXThreads, 2) k_pass_xc(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
+__global__ void __launch_bounds__(kXThreads, XcMinBlocks<P>::value) k_pass_xc(typename P::S* __restrict__ W, KgDev* __restrict__ dev,
                                                          double* __restrict__ part_sum, double* __restrict__ part_max,
                                                          const typename P::S* __restrict__ tw, double scale,
                                                          double lam) {
@@ -49,21 +60,26 @@ __global__ void __launch_bounds__(kXThreads, 2) k_pass_xc(typename P::S* __restr
     C v[8];
 #pragma unroll
     for (int s = 0; s < 8; s++) v[s] = P::load(L[j + T * s]);
-    fft<P, N>(v, j, tw, 1, lsm, +1);
+    // inverse transform, then (stepping pass) the forward one, through one copy of the code
+#pragma unroll 1
+    for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
+        fft<P, N>(v, j, tw, 1, lsm, dir == 0 ? +1 : -1);
+        if (dir == 0) {
 #pragma unroll
-    for (int s = 0; s < 8; s++) {
-        v[s].re = P::scale2(v[s].re, scale);   // scale = 1/N^3, a power of two
-        v[s].im = P::scale2(v[s].im, scale);
-        const R m2 = v[s].re * v[s].re + v[s].im * v[s].im;
-        st.take_sq(m2, want_sum);
-        if (MODE == MODE_STEP) {
-            const R g = rlam * m2;
-            v[s].re = g * v[s].re;
-            v[s].im = g * v[s].im;
+            for (int s = 0; s < 8; s++) {
+                v[s].re = P::scale2(v[s].re, scale);   // scale = 1/N^3, a power of two
+                v[s].im = P::scale2(v[s].im, scale);
+                const R m2 = v[s].re * v[s].re + v[s].im * v[s].im;
+                st.take_sq(m2, want_sum);
+                if (MODE == MODE_STEP) {
+                    const R g = rlam * m2;
+                    v[s].re = g * v[s].re;
+                    v[s].im = g * v[s].im;
+                }
+            }
         }
     }
     if (MODE == MODE_STEP) {
-        fft<P, N>(v, j, tw, 1, lsm, -1);
 #pragma unroll
         for (int s = 0; s < 8; s++) L[j + T * s] = P::pack(v[s]);
     }

@@ -212,7 +212,8 @@ struct XPaired<PrecDF> {
 };
 
 // resident CTAs per SM the x pass is compiled for: the paired double-float body fits
-// three (80 registers, no spills); the FP32 and FP64 bodies need more registers
+// four (64 registers, no spills; 1.61 -> 1.44 ms at 512^3 against two); the pipelined
+// FP32 body measured slower at three (0.48 -> 0.51 ms), and the FP64 body needs its registers
 template <class P>
 struct XMinBlocks {
     static constexpr int value = 2;
