@@ -202,8 +202,23 @@ __device__ __forceinline__ void block_exclusive_scan(int* a, int n) {
     __syncthreads();
 }
 
+// resident CTAs per SM the step kernel is compiled for (the autotuner picks up to this
+// many): the largest count with at most a few dozen bytes of spills
 template <class P>
-__global__ void __launch_bounds__(kEnsThreads, 2) k_ens_step(EnsParams p) {
+struct EnsMinBlocks {
+    static constexpr int value = 2;
+};
+template <>
+struct EnsMinBlocks<PrecDF> {
+    static constexpr int value = 3;
+};
+template <>
+struct EnsMinBlocks<PrecF32> {
+    static constexpr int value = 4;
+};
+
+template <class P>
+__global__ void __launch_bounds__(kEnsThreads, EnsMinBlocks<P>::value) k_ens_step(EnsParams p) {
     typedef typename P::S S;
     extern __shared__ __align__(16) unsigned char smraw[];
     S* sm = reinterpret_cast<S*>(smraw);
