@@ -202,7 +202,7 @@ struct LineSmemX {
 // (k = b mod Ns), takes the R-point DFT and writes y[(b - k) R + k + r Ns].
 // twmul: table length / n.
 // ---------------------------------------------------------------------------
-template <class P, int n, int STAGE, class SM>
+template <class P, int n, int STAGE, class SM, bool TWPOW = false>
 __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw,
                                           int twmul, SM& sm, int sg) {
     typedef cx<typename P::R> C;
@@ -221,8 +221,31 @@ __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, cons
 #pragma unroll
         for (int r = 0; r < RADIX; r++) u[r] = v[q + r * Q];
         if (Ns > 1) {
+            if constexpr (TWPOW && RADIX == 8) {
+                // one twiddle load per butterfly, the other six powers formed on the FMA
+                // pipe with at most three products in a chain (for a pass bound by the
+                // L1TEX pipe that the table loads go through)
+                const C w1 = twiddle<P>(tw, k * (n / (Ns * RADIX)) * twmul, sg);
+                const C w2 = cmul(w1, w1), w3 = cmul(w2, w1), w4 = cmul(w2, w2);
+                const C w5 = cmul(w4, w1), w6 = cmul(w4, w2), w7 = cmul(w4, w3);
+                u[1] = P::ctw(u[1], w1);
+                u[2] = P::ctw(u[2], w2);
+                u[3] = P::ctw(u[3], w3);
+                u[4] = P::ctw(u[4], w4);
+                u[5] = P::ctw(u[5], w5);
+                u[6] = P::ctw(u[6], w6);
+                u[7] = P::ctw(u[7], w7);
+            } else if constexpr (TWPOW && RADIX == 4) {
+                const C w1 = twiddle<P>(tw, k * (n / (Ns * RADIX)) * twmul, sg);
+                const C w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+                u[1] = P::ctw(u[1], w1);
+                u[2] = P::ctw(u[2], w2);
+                u[3] = P::ctw(u[3], w3);
+            } else {
 #pragma unroll
-            for (int r = 1; r < RADIX; r++) u[r] = P::ctw(u[r], twiddle<P>(tw, k * r * (n / (Ns * RADIX)) * twmul, sg));
+                for (int r = 1; r < RADIX; r++)
+                    u[r] = P::ctw(u[r], twiddle<P>(tw, k * r * (n / (Ns * RADIX)) * twmul, sg));
+            }
         }
         dft<P, RADIX, LAST>(u, sg);
         if (LAST) {
@@ -245,15 +268,16 @@ __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, cons
     }
 }
 
-// full length-n transform, unnormalised, sign sg; in and out: v[s] = x[j + T s]
-template <class P, int n, class SM>
+// full length-n transform, unnormalised, sign sg; in and out: v[s] = x[j + T s].
+// TWPOW: radix-8 stages form the twiddle powers by products instead of table loads
+template <class P, int n, class SM, bool TWPOW = false>
 __device__ __forceinline__ void fft(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw, int twmul,
                                     SM& sm, int sg) {
     typedef FftShape<n> Sh;
-    fft_stage<P, n, 0>(v, j, tw, twmul, sm, sg);
-    if constexpr (Sh::stages > 1) fft_stage<P, n, 1>(v, j, tw, twmul, sm, sg);
-    if constexpr (Sh::stages > 2) fft_stage<P, n, 2>(v, j, tw, twmul, sm, sg);
-    if constexpr (Sh::stages > 3) fft_stage<P, n, 3>(v, j, tw, twmul, sm, sg);
+    fft_stage<P, n, 0, SM, TWPOW>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 1) fft_stage<P, n, 1, SM, TWPOW>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 2) fft_stage<P, n, 2, SM, TWPOW>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 3) fft_stage<P, n, 3, SM, TWPOW>(v, j, tw, twmul, sm, sg);
 }
 
 // ---------------------------------------------------------------------------

@@ -58,7 +58,8 @@ __device__ __forceinline__ void x_line_body(const typename P::S* Lin, typename P
     // inverse transform, then (stepping pass) the forward one, through one copy of the code
 #pragma unroll 1
     for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
-        fft<P, M>(v, j, tw, 2, lsm, dir == 0 ? +1 : -1);
+        // the FP32 x pass is bound by the L1TEX pipe: twiddle powers by products there
+        fft<P, M, LineSmem<P>, sizeof(typename P::R) == 4>(v, j, tw, 2, lsm, dir == 0 ? +1 : -1);
         if (dir == 0) {
 #pragma unroll
             for (int s = 0; s < 8; s++) {
