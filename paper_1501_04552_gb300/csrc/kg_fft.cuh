@@ -69,6 +69,25 @@ __device__ __forceinline__ cx<typename P::R> twiddle(const typename P::S* __rest
     return w;
 }
 
+// w[s] = exp(sg 2 pi i (j + T s) / Ntab), s = 0..7, from two table loads and products
+// (chains of at most four products): for passes bound by the L1TEX pipe
+template <class P>
+__device__ __forceinline__ void twiddle_run(const typename P::S* __restrict__ tw, int j, int T, int sg,
+                                            cx<typename P::R> (&w)[8]) {
+    typedef cx<typename P::R> C;
+    const C wj = twiddle<P>(tw, j, sg), wt = twiddle<P>(tw, T, sg);
+    const C t2 = cmul(wt, wt), t3 = cmul(t2, wt), t4 = cmul(t2, t2);
+    const C t5 = cmul(t4, wt), t6 = cmul(t4, t2), t7 = cmul(t4, t3);
+    w[0] = wj;
+    w[1] = cmul(wj, wt);
+    w[2] = cmul(wj, t2);
+    w[3] = cmul(wj, t3);
+    w[4] = cmul(wj, t4);
+    w[5] = cmul(wj, t5);
+    w[6] = cmul(wj, t6);
+    w[7] = cmul(wj, t7);
+}
+
 // a * (sg i) = (-sg a.im, sg a.re)
 template <class P>
 __device__ __forceinline__ cx<typename P::R> mul_sgi(cx<typename P::R> a, int sg) {

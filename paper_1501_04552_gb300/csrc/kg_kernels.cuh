@@ -26,6 +26,9 @@ __device__ __forceinline__ void x_load_c2r(const typename P::S* line, int j, con
     typedef typename P::R R;
     typedef cx<R> C;
     constexpr int M = N / 2, T = XShape<N>::T;
+    constexpr bool kPow = sizeof(R) == 4;   // FP32: twiddles by products (L1TEX-bound pass)
+    C wr[8];
+    if constexpr (kPow) twiddle_run<P>(tw, j, T, +1, wr);
 #pragma unroll
     for (int s = 0; s < 8; s++) {
         const int k = j + T * s;
@@ -37,7 +40,7 @@ __device__ __forceinline__ void x_load_c2r(const typename P::S* line, int j, con
         }
         C A = P::cadd(X, conj(Xp));
         C B = P::csub(X, conj(Xp));
-        C w = twiddle<P>(tw, k, +1);       // exp(+2 pi i k / N)
+        const C w = kPow ? wr[s] : twiddle<P>(tw, k, +1);   // exp(+2 pi i k / N)
         v[s] = P::cnorm(P::cadd(A, mul_i(P::ctw(B, w))));
     }
 }
@@ -83,6 +86,9 @@ __device__ __forceinline__ void x_line_body(const typename P::S* Lin, typename P
         for (int s = 0; s < 8; s++) lsm.put(j + T * s, v[s]);
         lsm.sync();
         const double half = 0.5;
+        constexpr bool kPow = sizeof(R) == 4;
+        C wf[8];
+        if constexpr (kPow) twiddle_run<P>(tw, j, T, -1, wf);
 #pragma unroll
         for (int s = 0; s < 8; s++) {
             const int k = j + T * s;
@@ -90,7 +96,7 @@ __device__ __forceinline__ void x_line_body(const typename P::S* Lin, typename P
             C Zp = lsm.get((M - k) & (M - 1));
             C A = P::cadd(Z, conj(Zp));
             C B = P::csub(Z, conj(Zp));
-            C w = twiddle<P>(tw, k, -1);   // exp(-2 pi i k / N)
+            const C w = kPow ? wf[s] : twiddle<P>(tw, k, -1);   // exp(-2 pi i k / N)
             C D = mul_i(P::ctw(B, w));
             C out = P::cnorm(P::csub(A, D));
             out.re = P::scale2(out.re, half);
