@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(kXThreads, XcMinBlocks<P>::value) k_pass_xc(ty
     // inverse transform, then (stepping pass) the forward one, through one copy of the code
 #pragma unroll 1
     for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
-        fft<P, N>(v, j, tw, 1, lsm, dir == 0 ? +1 : -1);
+        // FP32: twiddle powers by products (the pass is bound by the L1TEX pipe)
+        fft<P, N, LineSmemX<P, X::CTA_SYNC>, sizeof(R) == 4>(v, j, tw, 1, lsm, dir == 0 ? +1 : -1);
         if (dir == 0) {
 #pragma unroll
             for (int s = 0; s < 8; s++) {
