@@ -46,9 +46,9 @@ PAPER_TABLE1 = [("Hornet", 12288, 0.319), ("Juqueen", 262144, 0.350), ("Stampede
 # DRAM bytes (read + write) per launch of a step kernel at 512^3, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; the capture is summarised under
 # profiles/), valid only for the kernel sources it was taken on: KERNEL_SOURCES hashed
-TRAFFIC_512 = {("df64", "x"): 2095183872, ("df64", "yf"): 2096257280, ("df64", "zf"): 2096838144,
-               ("df64", "update"): 5338650112, ("df64", "zi"): 2096741376, ("df64", "yi"): 2096777472}
-TRAFFIC_SOURCES_SHA = "61b7052462cea0bf"
+TRAFFIC_512 = {("df64", "x"): 2095851776, ("df64", "yf"): 2096619264, ("df64", "zf"): 2096815360,
+               ("df64", "update"): 5338190592, ("df64", "zi"): 2096896000, ("df64", "yi"): 2096212736}
+TRAFFIC_SOURCES_SHA = "d79f5ddeef038eb1"
 KERNEL_SOURCES = ["kg_arith.cuh", "kg_fft.cuh", "kg_kernels.cuh", "kg_complex.cuh", "kg_launch_impl.cuh"]
 
 
