@@ -19,6 +19,9 @@ def test_every_declared_symbol_is_exported(kg):
     assert len(names) >= 15
     for n in names:
         assert hasattr(kg.lib, n), n
+    # and the binding gives every entry point an explicit signature (ctypes defaults would
+    # pass doubles and sizes wrongly)
+    assert sorted(kg._sig) == names
 
 
 def test_calls_before_init_are_state_errors(kg):
