@@ -207,14 +207,18 @@ __device__ __forceinline__ void cp_async_elem(S* smem, const S* gmem) {
     }
 }
 
-// The double-float pass takes x-lines in pairs (x_pair_body): fewer FP32 operations
-// per point, which is what bounds it.
+// The double-float and FP64 passes take x-lines in pairs (x_pair_body): fewer
+// arithmetic operations per point, which is what bounds them.
 template <class P>
 struct XPaired {
     static constexpr bool value = false;
 };
 template <>
 struct XPaired<PrecDF> {
+    static constexpr bool value = true;
+};
+template <>
+struct XPaired<PrecF64> {
     static constexpr bool value = true;
 };
 
@@ -230,11 +234,11 @@ struct XMinBlocks<PrecDF> {
     static constexpr int value = 4;
 };
 
-// How pass X walks W.  Pipelined (FP32 and FP64 passes, bound by latency and by the
-// FP64 pipe): a persistent grid walks the batches, and while a CTA transforms one batch
-// from shared memory the next one lands in the other half of a double buffer
-// (cp.async).  Direct (double-float passes, bound by FP32 issue, where the copy loop and
-// the extra barriers cost more than they hide): one batch per CTA, loaded from global
+// How pass X walks W.  Pipelined (the FP32 pass, bound by latency and the L1TEX pipe): a
+// persistent grid walks the batches, and while a CTA transforms one batch from shared
+// memory the next one lands in the other half of a double buffer (cp.async).  Direct
+// (the double-float and FP64 passes, bound by their arithmetic pipes, where the copy loop
+// and the extra barriers cost more than they hide): one batch per CTA, loaded from global
 // memory straight into registers.
 template <class P>
 struct XPipelined {
@@ -242,6 +246,10 @@ struct XPipelined {
 };
 template <>
 struct XPipelined<PrecDF> {
+    static constexpr bool value = false;
+};
+template <>
+struct XPipelined<PrecF64> {
     static constexpr bool value = false;
 };
 
