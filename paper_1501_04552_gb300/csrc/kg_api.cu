@@ -286,7 +286,7 @@ int create_ctx(int N, double L, double dt, bool cplx, Ctx** out) {
         if (c->pl->x_parts(N) <= 0) KG_TRY(fail(KG_ECUDA, "x pass occupancy query failed"));
         c->nparts = std::max(std::max(c->pl->x_parts(N), c->pl->update_parts(N)), x_inverse_parts(N));
     }
-    c->nparts = std::max(c->nparts, 152 * 4);
+    c->nparts = std::max(c->nparts, kStrideCtas);   // the on-demand Q partials
     KG_TRY(dalloc(c, (void**)&c->part_sum, sizeof(double) * c->nparts, "partials"));
     KG_TRY(dalloc(c, (void**)&c->part_max, sizeof(double) * c->nparts, "partials max"));
     KG_TRY(dalloc(c, (void**)&c->part2, sizeof(double) * (c->nparts / 1024 + 1), "second-stage partials"));
@@ -599,7 +599,7 @@ int kg_energy(double* E) {
     } else {
         const double2* cur = d.phase ? c->S1 : c->S0;
         const double2* old = d.phase ? c->S0 : c->S1;
-        const int np = 152 * 4;
+        const int np = kStrideCtas;
         KG_CK(launch_energy_q(N, cur, old, c->w2, 1.0 / c->dt, c->part_sum, np, c->cplx, st));
         KG_CK(launch_fin_sum(c->part_sum, np, h * h * h * inv_n3(N), c->scal, st));
         KG_CK(cudaMemcpyAsync(&Q, c->scal, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -361,7 +361,7 @@ int kg_ens_init(int count, const int* Ns, double L, double dt, const double* A, 
         in.W = (void*)(bw + ow[i]);
         in.N = N;
         in.blowup_level = -1;
-        k_gaussian<<<152 * 4, 256, 0, e->stream>>>(e->phys, N, L, A[i], s[i]);
+        k_gaussian<<<kStrideCtas, 256, 0, e->stream>>>(e->phys, N, L, A[i], s[i]);
         if (cudaGetLastError() != cudaSuccess) KG_ETRY(efail(KG_ECUDA, "gaussian launch"));
         // F^0 scratch: W itself when it holds 16-byte values, else the spectral scratch
         double2* fbuf = e->pl->store_bytes == sizeof(double2) ? (double2*)in.W : e->tmp;

@@ -40,8 +40,8 @@ int x_inverse_parts(int N) { return N * N / (kXThreads / (N / 16)); }
 cudaError_t launch_startup(int N, const double2* a, double2* b, const double2* f, const double2* coef, double dt,
                            bool cplx, cudaStream_t st) {
     KG_DISPATCH_N(N, {
-        if (cplx) k_startup<NN, true><<<152 * 8, 256, 0, st>>>(a, b, f, coef, dt);
-        else k_startup<NN, false><<<152 * 8, 256, 0, st>>>(a, b, f, coef, dt);
+        if (cplx) k_startup<NN, true><<<kStrideCtasDeep, 256, 0, st>>>(a, b, f, coef, dt);
+        else k_startup<NN, false><<<kStrideCtasDeep, 256, 0, st>>>(a, b, f, coef, dt);
         return cudaGetLastError();
     });
 }

@@ -8,6 +8,11 @@
 
 namespace kg {
 
+// grid sizes of the grid-stride kernels (any count is correct; these fill a 152-SM GB300
+// four or eight CTAs deep)
+constexpr int kStrideCtas = 152 * 4;
+constexpr int kStrideCtasDeep = 152 * 8;
+
 struct KgDev;
 struct EnsParams;
 
