@@ -171,3 +171,25 @@ def test_large_field_finiteness_check_on_the_host(kg):
         u[pos] = -np.inf
         assert kg.lib.kg_init(N, 32.0, 0.01, u.ctypes.data, None) == kg.KG_EINVAL
         u[pos] = 0.0
+
+
+def test_ensemble_and_network_arguments_rejected_on_the_host(kg):
+    ok_N = np.array([64, 128], dtype=np.int32)
+    A = np.array([1.0, 2.0])
+    s = np.array([1.0, 1.5])
+    lib = kg.lib
+    assert lib.kg_ens_init(0, ok_N.ctypes.data, 32.0, 0.005, A.ctypes.data, s.ctypes.data) == kg.KG_EINVAL
+    assert lib.kg_ens_init(1025, ok_N.ctypes.data, 32.0, 0.005, A.ctypes.data, s.ctypes.data) == kg.KG_EINVAL
+    assert lib.kg_ens_init(2, None, 32.0, 0.005, A.ctypes.data, s.ctypes.data) == kg.KG_EINVAL
+    assert lib.kg_ens_init(2, ok_N.ctypes.data, 32.0, -1.0, A.ctypes.data, s.ctypes.data) == kg.KG_EINVAL
+    bad_N = np.array([64, 96], dtype=np.int32)
+    assert lib.kg_ens_init(2, bad_N.ctypes.data, 32.0, 0.005, A.ctypes.data, s.ctypes.data) == kg.KG_ENOTSUP
+    bad_A = np.array([1.0, np.nan])
+    assert lib.kg_ens_init(2, ok_N.ctypes.data, 32.0, 0.005, bad_A.ctypes.data, s.ctypes.data) == kg.KG_EINVAL
+    bad_s = np.array([1.0, 0.0])
+    assert lib.kg_ens_init(2, ok_N.ctypes.data, 32.0, 0.005, A.ctypes.data, bad_s.ctypes.data) == kg.KG_EINVAL
+    # calls that need an ensemble or a network before one exists
+    done = C.c_longlong()
+    ms = C.c_double()
+    lib.kg_ens_finalize()
+    assert lib.kg_ens_run(10, 0.0, C.byref(done), C.byref(ms)) == kg.KG_ESTATE
