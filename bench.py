@@ -31,7 +31,8 @@ L_BOX = 32.0
 DT = 0.005
 ENERGY_EVERY = 10
 PRECISION = "df64"
-STEP_LAUNCHES = 9
+STEP_LAUNCHES = 7
+E2E_REPEATS = 3
 METRIC = "512^3 KG steps/s"
 S_BYTES = N_GRID * N_GRID * (N_GRID // 2 + 1) * 16      # one complex128 half-spectrum array
 
@@ -46,9 +47,9 @@ PAPER_TABLE1 = [("Hornet", 12288, 0.319), ("Juqueen", 262144, 0.350), ("Stampede
 # DRAM bytes (read + write) per launch of a step kernel at 512^3, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; the capture is summarised under
 # profiles/), valid only for the kernel sources it was taken on: KERNEL_SOURCES hashed
-TRAFFIC_512 = {("df64", "x"): 2095451648, ("df64", "yf"): 2096257792, ("df64", "zf"): 2096747008,
-               ("df64", "update"): 5338596352, ("df64", "zi"): 2096843520, ("df64", "yi"): 2096246016}
-TRAFFIC_SOURCES_SHA = "7c5874c76d4244d2"
+TRAFFIC_512 = {("df64", "x"): 2095011328, ("df64", "yf"): 2096729088, ("df64", "z"): 5658179840,
+               ("df64", "yi"): 2096259328}
+TRAFFIC_SOURCES_SHA = "c34c9e941255def7"
 KERNEL_SOURCES = ["kg_arith.cuh", "kg_fft.cuh", "kg_kernels.cuh", "kg_complex.cuh", "kg_launch_impl.cuh"]
 
 
@@ -73,8 +74,22 @@ def algorithmic_bytes(prec, n=N_GRID):
     plus reading uh^n, uh^{n-1} and writing uh^{n+1} (11 S, or 7 S with FP32 W)"""
     s_bytes = n * n * (n // 2 + 1) * 16
     w = s_bytes if prec in ("fp64", "df64") else s_bytes // 2
-    per_kernel = {"x": 2 * w, "yf": 2 * w, "zf": 2 * w, "update": 2 * w + 3 * s_bytes, "zi": 2 * w, "yi": 2 * w}
+    per_kernel = {"x": 2 * w, "yf": 2 * w, "zf": 2 * w, "update": 2 * w + 3 * s_bytes, "zi": 2 * w, "yi": 2 * w,
+                  "z": 2 * w + 3 * s_bytes}
     return per_kernel, 8 * w + 3 * s_bytes
+
+
+def kernel_groups(k_ms):
+    """names and device ms of a step's kernel groups from kg_step_timed: x, yf, z (the
+    fused z pass: forward z FFT, update, inverse z FFT), yi when the update and inverse-z
+    slots are empty; else the six separate groups"""
+    from paper_1501_04552_gb300 import kg
+    if k_ms[3] == 0.0 and k_ms[4] == 0.0:
+        return ["x", "yf", "z", "yi"], [k_ms[0], k_ms[1], k_ms[2], k_ms[5]]
+    return list(kg.STEP_KERNELS), list(k_ms)
+
+
+KERNEL_NAMES = {"x": "k_pass_x", "z": "k_zstep", "update": "k_update"}
 
 
 # FP32 issue peak of the GPU: 152 SMs x 128 FP32 lanes x 2.07 GHz (max SM clock), one
@@ -289,8 +304,7 @@ def main():
     value = replicas.throughput(args.steps, world, ms * 1e-3)
 
     # per-kernel device times (CUDA events on the library's stream) for the roofline
-    names = kg.STEP_KERNELS
-    k_avg = [t / args.steps for t in kg.kg_step_timed(args.steps)]
+    names, k_avg = kernel_groups([t / args.steps for t in kg.kg_step_timed(args.steps)])
     k_bytes, step_bytes = algorithmic_bytes(prec, NG)
     dom = int(np.argmax(k_avg))
     peak, peak_kind = peaks()
@@ -298,8 +312,7 @@ def main():
     step_achieved = step_bytes / (ms_per_step * 1e-3) / 1e9
     per_kernel = {n: {"ms": round(t, 4), "GBps": round(k_bytes[n] / (t * 1e-3) / 1e9, 1),
                       "frac": round(k_bytes[n] / (t * 1e-3) / 1e9 / peak, 4)} for n, t in zip(names, k_avg)}
-    roofline = {"bound": "hbm", "kernel": "k_pass_x" if names[dom] == "x" else
-                ("k_update" if names[dom] == "update" else "k_col(%s)" % names[dom]),
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES.get(names[dom], "k_col(%s)" % names[dom]),
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": measured_traffic(prec, names[dom], NG), "peak_kind": peak_kind,
                 "step_achieved": round(step_achieved, 1), "step_frac": round(step_achieved / peak, 4),
@@ -310,8 +323,9 @@ def main():
     roofline_alu = None
     if prec == "df64" and NG == 512:
         ops = df64_fp32_ops(NG)
-        per = {n: {"ops": ops["x" if n == "x" else "col"],
-                   "frac": round(ops["x" if n == "x" else "col"] / (t * 1e-3) / FP32_ISSUE_PEAK, 4)}
+        # the fused z pass: two column transforms (its update runs on the FP64 pipe)
+        kops = {n: ops["x"] if n == "x" else (2 * ops["col"] if n == "z" else ops["col"]) for n in names}
+        per = {n: {"ops": kops[n], "frac": round(kops[n] / (t * 1e-3) / FP32_ISSUE_PEAK, 4)}
                for n, t in zip(names, k_avg) if n != "update"}
         x_rate = ops["x"] / (k_avg[names.index("x")] * 1e-3)
         roofline_alu = {"bound": "alu", "kernel": "k_pass_x", "achieved": round(x_rate / 1e12, 2),
@@ -324,17 +338,22 @@ def main():
     pinned_u0 = torch.from_numpy(u0).pin_memory()
     out = torch.empty((NG,) * 3, dtype=torch.float64).pin_memory()
     kg.kg_set_options(precision=prec, energy_every=ENERGY_EVERY)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    kg.lib.kg_init(NG, L_BOX, DT, pinned_u0.data_ptr(), None)
-    kg.kg_step(args.steps)
-    kg.lib.kg_fetch(out.data_ptr())
-    torch.cuda.synchronize()
-    t_e2e = replicas.max_over_ranks(time.perf_counter() - t0, device=f"cuda:{local}")
+    e2e_runs = []
+    for _ in range(E2E_REPEATS):     # host-side phases vary from run to run: the median is reported
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kg.lib.kg_init(NG, L_BOX, DT, pinned_u0.data_ptr(), None)
+        kg.kg_step(args.steps)
+        kg.lib.kg_fetch(out.data_ptr())
+        torch.cuda.synchronize()
+        e2e_runs.append(replicas.max_over_ranks(time.perf_counter() - t0, device=f"cuda:{local}"))
+    t_e2e = sorted(e2e_runs)[len(e2e_runs) // 2]
     e2e = {"value": replicas.throughput(args.steps, world, t_e2e), "unit": "steps/s",
+           "runs_s": [round(t, 4) for t in e2e_runs],
            "h2d_bytes_per_step": u0.nbytes // args.steps, "d2h_bytes_per_step": out.numel() * 8 // args.steps,
-           "what": "kg_init from pinned host u0 + %d steps + kg_fetch to pinned host" % args.steps}
+           "what": "kg_init from pinned host u0 + %d steps + kg_fetch to pinned host; median of %d runs"
+                   % (args.steps, E2E_REPEATS)}
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -343,10 +362,10 @@ def main():
                 continue
             steps = ENERGY_EVERY * max(1, args.steps // (8 if other == "fp64" else 1) // ENERGY_EVERY)
             o_ms = timed_steps(other, steps, ENERGY_EVERY)
-            o_k = [t / steps for t in kg.kg_step_timed(steps)]
+            o_names, o_k = kernel_groups([t / steps for t in kg.kg_step_timed(steps)])
             o_bytes, o_step_bytes = algorithmic_bytes(other, NG)
             extras[other] = {"steps_per_s": round(steps / (o_ms * 1e-3), 2), "ms_per_step": round(o_ms / steps, 4),
-                             "kernel_ms": {n: round(t, 4) for n, t in zip(names, o_k)},
+                             "kernel_ms": {n: round(t, 4) for n, t in zip(o_names, o_k)},
                              "step_hbm_frac": round(o_step_bytes / (o_ms / steps * 1e-3) / 1e9 / peak, 4)}
         extras["cufft_torch"] = torch_fft_point(u0, local)
         if NG == 512:
@@ -439,13 +458,13 @@ def complex_point(kg, stream, torch, u0, NG, local, prec, peak):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    k_ms = [t / steps for t in kg.kg_step_timed(steps)]
+    k_names, k_ms = kernel_groups([t / steps for t in kg.kg_step_timed(steps)])
     sc = NG ** 3 * 16
     w = sc if prec in ("fp64", "df64") else sc // 2
     step_bytes = 8 * w + 3 * sc
     kg.kg_finalize()
     return {"steps_per_s": round(1e3 / ms, 2), "ms_per_step": round(ms, 4),
-            "kernel_ms": {n: round(t, 4) for n, t in zip(kg.STEP_KERNELS, k_ms)},
+            "kernel_ms": {n: round(t, 4) for n, t in zip(k_names, k_ms)},
             "step_hbm_frac": round(step_bytes / (ms * 1e-3) / 1e9 / peak, 4)}
 
 

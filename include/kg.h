@@ -110,8 +110,10 @@ int kg_fetch_spectral(double* a, double* b);
 
 /* Instrumentation: enqueue n steps launching each kernel separately, timing them
  * with CUDA events on the context's stream; ms[0..5] receive the summed device time
- * of the x pass (with its finaliser), forward y, forward z, the update (with its
- * finaliser), inverse z and inverse y.  Synchronises. */
+ * of the x pass (with its finaliser), forward y, the z pass, its update part, its
+ * inverse-z part and inverse y.  The z pass (forward z FFT, update, inverse z FFT) is
+ * one kernel, so ms[2] holds all of it with its finaliser and ms[3], ms[4] receive 0.
+ * Synchronises. */
 int kg_step_timed(int n, float* ms);
 
 /* Bytes of device memory the context holds. */

@@ -10,10 +10,10 @@
 //        (One line through an N/2-point complex FFT, or two lines through one N-point
 //        complex FFT.)
 //   Yf : per (z, kx) column, forward complex FFT along y, in place.
-//   Zf : per (ky, kx) column, forward complex FFT along z -> F^n_k, in place.
-//   U  : per mode, the FP64 update uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k
-//        written over uh^{n-1} and into W; optional Q^{n+1/2} partial sums.
-//   Zi : per (ky, kx) column, inverse complex FFT along z, in place.
+//   Z  : per (ky, kx) column, forward complex FFT along z -> F^n_k; per mode, the FP64
+//        update uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k written over uh^{n-1},
+//        optional Q^{n+1/2} partial sums; inverse complex FFT along z of uh^{n+1}, in
+//        place (one kernel; the IEEE FP64 passes run the three parts as kernels Zf, U, Zi).
 //   Yi : per (z, kx) column, inverse complex FFT along y, in place.
 //
 // The pencil transposes of a distributed 3D FFT become strided column accesses:

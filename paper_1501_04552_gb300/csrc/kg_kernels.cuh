@@ -513,20 +513,21 @@ constexpr int kUpdThreads = 256;
 constexpr int kSumThreads = 1024;   // second reduction stage of the update's Q partials
 
 // One term of Q^{n+1/2} without its constant factor 1/(2 dt^2):
-//     w_k ( |a1 - a0|^2 + r_k |a1 + a0|^2 ),   r_k = dt^2 omega_k^2 / 4,
-// (the Q definition of kg.h multiplied by 2 dt^2).  The differences and sums of the two
-// levels are formed in FP64 (a1 - a0 cancels); the squares and their sums are formed in
-// double-float on the FP32 pipe, except for the IEEE FP64 passes, which stay in FP64.
+//     w_k ( |a1 - a0|^2 + r_k |a1 + a0|^2 ),   r_k = qr omega_k^2,  qr = dt^2 / 4,
+// (the Q definition of kg.h multiplied by 2 dt^2).  Only the cancelling differences
+// a1 - a0 are formed in FP64; the sums a1 + a0, r_k, the squares and their sums are
+// formed in double-float on the FP32 pipe (the FP64 pipe already carries the update),
+// except for the IEEE FP64 passes, which stay in FP64.
 template <class P>
 struct QTerm {
     typedef df T;
     static __device__ __forceinline__ T zero() { return df_make(0.f, 0.f); }
-    static __device__ __forceinline__ T term(double n_re, double n_im, double2 a, double r, bool twice) {
+    static __device__ __forceinline__ T term(double n_re, double n_im, double2 a, double w2, double qr, bool twice) {
         const df dre = d2df_int(n_re - a.x), dim = d2df_int(n_im - a.y);
-        const df sre = d2df_int(n_re + a.x), sim = d2df_int(n_im + a.y);
+        const df sre = d2df_int(n_re) + d2df_int(a.x), sim = d2df_int(n_im) + d2df_int(a.y);
         const df D = dre * dre + dim * dim;
         const df S = sre * sre + sim * sim;
-        df t = D + d2df_int(r) * S;
+        df t = D + (d2df_int(w2) * d2df_int(qr)) * S;
         return twice ? df_scale2(t, 2.0f) : t;
     }
     static __device__ __forceinline__ T add(T x, T y) { return x + y; }
@@ -539,7 +540,8 @@ template <>
 struct QTerm<PrecF64> {
     typedef double T;
     static __device__ __forceinline__ T zero() { return 0.0; }
-    static __device__ __forceinline__ T term(double n_re, double n_im, double2 a, double r, bool twice) {
+    static __device__ __forceinline__ T term(double n_re, double n_im, double2 a, double w2, double qr, bool twice) {
+        const double r = qr * w2;
         const double dre = n_re - a.x, dim = n_im - a.y, sre = n_re + a.x, sim = n_im + a.y;
         const double t = fma(r, fma(sre, sre, sim * sim), fma(dre, dre, dim * dim));
         return twice ? t + t : t;
@@ -597,11 +599,101 @@ __global__ void __launch_bounds__(kUpdThreads, 6) k_update(typename P::S* __rest
         const double nim = P::fma_into(cf.y, f.im, fma(cf.x, a.y, -b.y));
         if (update) old[i] = make_double2(nre, nim);
         W[i] = P::pack(cmake<R>(P::from_f64(nre), P::from_f64(nim)));
-        if (want_q) q = Q::term(nre, nim, a, qr * __ldg(w2tab + mi.m2), mi.twice);
+        if (want_q) q = Q::term(nre, nim, a, __ldg(w2tab + mi.m2), qr, mi.twice);
     }
     if (want_q) {
         q = block_tree_sum<Q, kUpdThreads>(q, red);
         if (threadIdx.x == 0) part_sum[blockIdx.x] = qc * Q::value(q);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z pass of the single-state step in one kernel: per (ky, kx) column, the forward z
+// FFT -> F^n_k, the update of k_update (uh^{n+1} over uh^{n-1}, W <- uh^{n+1} in the pass
+// precision, Q terms on recording steps), then the inverse z FFT of uh^{n+1}.  One pass
+// over W: 2 W + 3 S per launch instead of 6 W + 3 S for the three kernels.  The state
+// rows are read with plain loads after the forward transform (staging them in shared
+// memory by cp.async before it cost more occupancy than it hid latency).
+// C columns of N rows per CTA; C = 8 (128-byte double-float rows, 64-byte FP32 rows),
+// 16 at N = 16 so that a CTA is at least one warp.
+// ---------------------------------------------------------------------------
+template <int N>
+struct ZStepShape {
+    static constexpr int C = N >= 32 ? 8 : 16;
+    static constexpr int NT = C * N / 8;
+};
+// resident threads per SM the kernel is compiled for: 1024 (64 registers; the
+// double-float body spills a little there and is still faster than at 512 threads)
+template <class P, int N>
+struct ZStepMinBlocks {
+    static constexpr int kThreads = 1024;
+    static constexpr int value = kThreads / ZStepShape<N>::NT > 1 ? kThreads / ZStepShape<N>::NT : 1;
+};
+
+template <class P, int N, bool CPLX = false>
+__global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value)
+    k_zstep(typename P::S* __restrict__ W, double2* S0, double2* S1, KgDev* __restrict__ dev,
+            double* __restrict__ part_sum, const typename P::S* __restrict__ tw, const double2* __restrict__ coef,
+            const double* __restrict__ w2tab, double qr, double qc) {
+    typedef typename P::R R;
+    typedef typename P::S S;
+    typedef QTerm<P> Q;
+    constexpr int T = N / 8, C = ZStepShape<N>::C, NT = ZStepShape<N>::NT;
+    constexpr int NX = CPLX ? N : N / 2 + 1;   // columns per plane
+    extern __shared__ __align__(16) unsigned char smraw[];
+    S* sm = reinterpret_cast<S*>(smraw);
+    __shared__ typename Q::T red[NT / 32];
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const int kx = blockIdx.x * C + c, ky = blockIdx.y;
+    const bool valid = kx < NX;   // columns of the last tile beyond the plane compute on zeros
+    ColSmem<P, C> csm{sm, c};
+    tw = stage_table(tw, sm + N * C, N);
+    const bool want_q = kg_recording(dev);
+    const bool update = dev->frozen == 0;
+    const double2* __restrict__ cur = dev->phase ? S1 : S0;
+    double2* __restrict__ old = dev->phase ? S0 : S1;
+    const size_t rs = (size_t)N * NX, base = (size_t)ky * NX + kx;
+
+    cx<R> v[8];
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        if (valid) v[s] = P::load(W[base + (size_t)(j + T * s) * rs]);
+        else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
+    }
+    typename Q::T q = Q::zero();
+    // the 16-byte bodies are large: both transforms run through one copy of the FFT code
+    constexpr bool kShare = sizeof(S) == 16;
+#pragma unroll(kShare ? 1 : 2)
+    for (int dir = 0; dir < 2; dir++) {
+        fft<P, N>(v, j, tw, 1, csm, dir == 0 ? -1 : +1);
+        if (dir == 1) break;
+        const int mx = (CPLX && kx > N / 2) ? kx - N : kx;
+        const int my = ky <= N / 2 ? ky : ky - N;
+        const int mxy2 = mx * mx + my * my;
+        const bool twice = !CPLX && kx != 0 && kx != N / 2;
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            const int kz = j + T * s;
+            const int mz = kz <= N / 2 ? kz : kz - N;
+            const int m2 = mxy2 + mz * mz;
+            if (valid) {
+                const size_t idx = base + (size_t)kz * rs;
+                const double2 a = cur[idx], b = old[idx], cf = __ldg(coef + m2);
+                const double nre = P::fma_into(cf.y, v[s].re, fma(cf.x, a.x, -b.x));
+                const double nim = P::fma_into(cf.y, v[s].im, fma(cf.x, a.y, -b.y));
+                if (update) old[idx] = make_double2(nre, nim);
+                if (want_q) q = Q::add(q, Q::term(nre, nim, a, __ldg(w2tab + m2), qr, twice));
+                v[s] = cmake<R>(P::from_f64(nre), P::from_f64(nim));
+            }
+        }
+    }
+    if (valid) {
+#pragma unroll
+        for (int s = 0; s < 8; s++) W[base + (size_t)(j + T * s) * rs] = P::pack(v[s]);
+    }
+    if (want_q) {
+        q = block_tree_sum<Q, NT>(q, red);
+        if (threadIdx.x == 0) part_sum[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = qc * Q::value(q);
     }
 }
 

@@ -49,6 +49,12 @@ struct PassLaunch {
     cudaError_t (*updatec)(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum,
                            const double2* coef, const double* w2tab, double inv_dt, cudaStream_t st);
     int (*updatec_parts)(int N);
+    // the z pass in one kernel: forward z FFT, update (as update / updatec), inverse z
+    // FFT, of a real (cplx = false) or complex field; zstep_parts(N, cplx) Q partials.
+    // NULL where the step runs forward z, update and inverse z as three kernels.
+    cudaError_t (*zstep)(int N, bool cplx, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum,
+                         const void* tw, const double2* coef, const double* w2tab, double inv_dt, cudaStream_t st);
+    int (*zstep_parts)(int N, bool cplx);
 };
 
 extern const PassLaunch kLaunchF64;

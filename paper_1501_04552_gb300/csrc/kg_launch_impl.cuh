@@ -183,6 +183,33 @@ struct Launchers {
         });
     }
 
+    // fused z pass (forward z FFT, update, inverse z FFT) of a real (cplx = false) or
+    // complex field; zstep_parts: the Q partials it writes when recording
+    template <int N, bool CPLX>
+    static cudaError_t zstep_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const void* tw,
+                               const double2* coef, const double* w2, double inv_dt, cudaStream_t st) {
+        typedef ZStepShape<N> Z;
+        constexpr int NX = CPLX ? N : N / 2 + 1;
+        const size_t smem = (size_t)(N * Z::C + N) * sizeof(S);
+        auto kern = k_zstep<P, N, CPLX>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        const double qr = 0.25 / (inv_dt * inv_dt), qc = 0.5 * inv_dt * inv_dt;
+        dim3 grid((NX + Z::C - 1) / Z::C, N);
+        kern<<<grid, Z::NT, smem, st>>>((S*)W, S0, S1, dev, ps, (const S*)tw, coef, w2, qr, qc);
+        return cudaGetLastError();
+    }
+    static cudaError_t zstep(int N, bool cplx, void* W, double2* S0, double2* S1, KgDev* dev, double* ps,
+                             const void* tw, const double2* coef, const double* w2, double inv_dt, cudaStream_t st) {
+        if (cplx) { KG_DISPATCH_N(N, return (zstep_n<NN, true>(W, S0, S1, dev, ps, tw, coef, w2, inv_dt, st))); }
+        KG_DISPATCH_N(N, return (zstep_n<NN, false>(W, S0, S1, dev, ps, tw, coef, w2, inv_dt, st)));
+    }
+    static int zstep_parts(int N, bool cplx) {
+        const int C = N >= 32 ? ZStepShape<32>::C : ZStepShape<16>::C;
+        const int nx = cplx ? N : N / 2 + 1;
+        return (nx + C - 1) / C * N;
+    }
+
     static size_t ens_smem() {
         typedef EnsUnits<P, 64> U64;
         typedef EnsUnits<P, 128> U128;

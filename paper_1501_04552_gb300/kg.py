@@ -242,11 +242,13 @@ def kg_fetch_spectral(N):
     return a, b
 
 
-STEP_KERNELS = ["x", "yf", "zf", "update", "zi", "yi"]
+# slots of kg_step_timed: the z pass is one kernel, so "z" holds all of it and the
+# "update" and "zi" slots read 0
+STEP_KERNELS = ["x", "yf", "z", "update", "zi", "yi"]
 
 
 def kg_step_timed(n):
-    """summed device ms of the six kernel groups of a step (names in STEP_KERNELS)"""
+    """summed device ms of the kernel groups of a step (slot names in STEP_KERNELS)"""
     ms = (C.c_float * 6)()
     _check(lib.kg_step_timed(int(n), ms), "kg_step_timed")
     return [ms[i] for i in range(6)]

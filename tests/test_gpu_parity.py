@@ -314,3 +314,25 @@ def test_linear_mode_large_dt(kg, prec):
     ref = math.cos(n * th) * u0 + dt * b * math.sin(n * th) / math.sin(th) * I.plane_wave(N, L, m, "sin")
     assert np.abs(kg.kg_fetch(N) - ref).max() <= (1e-12 if prec != "mixed" else 1e-5)
     kg.kg_set_options()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_timed_steps_match_graph_steps(kg, prec):
+    """kg_step_timed launches the same kernels as the graph kg_step replays: the same
+    state bit for bit; the z pass is one kernel in the double-float and FP32 passes
+    (its update and inverse-z slots read 0) and three in the IEEE FP64 passes"""
+    N, dt = 64, 0.01
+    u0, v0 = smooth_ic(N, seed=3)
+    kg.kg_set_options(precision=prec, energy_every=4)
+    kg.kg_init(N, L, dt, u0, v0)
+    kg.kg_step(12)
+    ref_u, ref_E = kg.kg_fetch(N), kg.kg_energy()
+    kg.kg_init(N, L, dt, u0, v0)
+    ms = kg.kg_step_timed(12)
+    assert kg.kg_status()["level"] == 12
+    assert np.array_equal(kg.kg_fetch(N), ref_u) and kg.kg_energy() == ref_E
+    fused = prec != "fp64"
+    assert all(t > 0 for i, t in enumerate(ms) if not (fused and i in (3, 4)))
+    if fused:
+        assert ms[3] == 0.0 and ms[4] == 0.0
+    kg.kg_set_options()
