@@ -46,7 +46,7 @@ extern "C" {
 /* status codes */
 #define KG_OK 0
 #define KG_EINVAL (-1)    /* bad argument: NULL pointer, non-finite input, dt <= 0, ... */
-#define KG_ENOTSUP (-2)   /* N outside the supported set */
+#define KG_ENOTSUP (-2)   /* N outside the supported set, or a combination this build lacks */
 #define KG_ENOMEM (-3)    /* device or host allocation failed; nothing is leaked */
 #define KG_ECUDA (-4)     /* a CUDA runtime call failed; see kg_last_error() */
 #define KG_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
@@ -99,6 +99,27 @@ int kg_set_stream(void* stream);
 
 int kg_set_options(const kg_options* opt);  /* copies *opt; precision applies at the next init */
 int kg_get_options(kg_options* opt);
+
+/* ---- time-stepping scheme (section 3 names higher-order time stepping as future work
+ * and gives no scheme; the fourth-order one here is an outside specification) ----
+ * KG_SCHEME_EQ2 (default): Eq. (2).
+ * KG_SCHEME_COMPOSED4: Eq. (2) written as the equivalent one-step kick-drift-kick map on
+ * (uh, velocity) -- per mode p += (h/2) G_h(uh), uh += h p, p += (h/2) G_h(uh), with
+ * G_h = (F - omega^2 uh) / (1 + omega^2 h^2/4), which with h = dt is exactly Eq. (2) and its
+ * startup level -- composed as Yoshida's triple jump (Phys. Lett. A 150 (1990) 262): a step
+ * of length dt is three substeps of lengths g1 dt, g2 dt, g1 dt, g1 = 1/(2 - 2^{1/3}),
+ * g2 = 1 - 2 g1.  Fourth order in dt; one step costs three evaluations of F (three passes
+ * of the step's kernels; adjacent half kicks are merged).  kg_step(n) advances n steps and
+ * kg_status reports steps; the blow-up check and the max |u| of kg_status look at the
+ * field at integer steps only.  Real fields only (kg_init_complex: KG_ENOTSUP);
+ * energy_every and drift_tol must be 0 (kg_init: KG_EINVAL) and kg_energy returns
+ * KG_ENOTSUP.  kg_fetch_spectral returns (uh^n, P^n) where the stored velocity variable is
+ * P^n = p^n - (g1 dt/2) G_{g1 dt}(uh^n).  The scheme takes effect at the next kg_init (or
+ * comes from the checkpoint in kg_load_state). */
+#define KG_SCHEME_EQ2 0
+#define KG_SCHEME_COMPOSED4 1
+int kg_set_scheme(int scheme);   /* KG_EINVAL for an unknown scheme */
+int kg_get_scheme(int* scheme);  /* the scheme the next kg_init uses */
 
 /* Current level n, blow-up state (1 if frozen, with the level it froze at) and the
  * max |u| seen by the last step (that of u^{n-1}).  Synchronises. */
@@ -170,7 +191,7 @@ typedef struct kg_state_header {
     unsigned long long payload_bytes;   /* 2 * 16 * N*N*(N/2+1) (complex field: 2 * 16 * N^3) */
     unsigned long long checksum;        /* kg_state_checksum of the payload */
     int complex_field;                  /* 1: complex field (payload 2 * 16 * N^3 bytes) */
-    int pad1;
+    int scheme;                         /* KG_SCHEME_EQ2 or KG_SCHEME_COMPOSED4 */
     unsigned char reserved[256 - 168];  /* zero */
 } kg_state_header;
 
@@ -181,9 +202,9 @@ typedef struct kg_state_header {
 int kg_save_state(void* h, size_t cap, size_t* used);
 
 /* Replace the context by the checkpoint in h (len bytes): the run's grid, time
- * step and options (precision, energy_every, nonlinearity, blowup_threshold,
- * drift_tol) become the current ones, as kg_init plus kg_set_options would make
- * them, and the level, blow-up state and recorded energies are restored.  The
+ * step, scheme and options (precision, energy_every, nonlinearity, blowup_threshold,
+ * drift_tol) become the current ones, as kg_init plus kg_set_options and
+ * kg_set_scheme would make them, and the level, blow-up state and recorded energies are restored.  The
  * header and the payload checksum are checked before anything is replaced.
  * Errors: KG_EINVAL (bad magic, version, size, field or checksum) and KG_ENOTSUP
  * keep the old context and options; after KG_ENOMEM or KG_ECUDA no context remains

@@ -69,6 +69,9 @@ struct Ctx {
     double2* tw64 = nullptr; // same in FP64 for set-up and read-out
     double2* coef = nullptr; // (2 c, 2 beta) by integer m^2
     double* w2 = nullptr;    // omega^2 by integer m^2
+    int scheme = KG_SCHEME_EQ2;
+    double2* kick = nullptr; // composed scheme: merged-kick tables [3][m2max + 1]
+    double c4h[3] = {0.0, 0.0, 0.0};   // composed scheme: substep lengths
     std::vector<void*> allocs;
     size_t bytes = 0;
     bool have_E0 = false;
@@ -80,6 +83,7 @@ struct Ctx {
 
 Ctx* g_ctx = nullptr;
 kg_options g_opt = {KG_DF64, 0, 1.0, 0.0, 0.0};
+int g_scheme = KG_SCHEME_EQ2;
 cudaStream_t g_user_stream = nullptr;
 
 cudaStream_t stream_of(const Ctx* c) { return g_user_stream ? g_user_stream : c->own_stream; }
@@ -124,6 +128,11 @@ int upload_tables(Ctx* c) {
     c->tw64 = t.tw64;
     c->coef = t.coef;
     c->w2 = t.w2;
+    if (!c->cplx) {
+        rc = make_kick_tables(c->N, c->L, c->dt, [c](void** p, size_t b, const char* w) { return dalloc(c, p, b, w); },
+                              &c->kick, c->c4h);
+        if (rc) return rc;
+    }
     return KG_OK;
 }
 
@@ -220,9 +229,11 @@ int reuse_ctx(Ctx* c, double L, double dt, Ctx** out) {
     release(c, c->tw64, sizeof(double2) * N);
     release(c, c->coef, sizeof(double2) * (m2max + 1));
     release(c, c->w2, sizeof(double) * (m2max + 1));
+    if (c->kick) release(c, c->kick, sizeof(double2) * 3 * (m2max + 1));
     c->tw = c->tw64 = nullptr;
     c->coef = nullptr;
     c->w2 = nullptr;
+    c->kick = nullptr;
     c->L = L;
     c->dt = dt;
     c->lam = g_opt.nonlinearity;
@@ -320,6 +331,8 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
     int rc = check_grid(N, L, dt);
     if (rc) return rc;
     if (!u0) return fail(KG_EINVAL, "u0 is NULL");
+    if (g_scheme == KG_SCHEME_COMPOSED4 && (g_opt.energy_every != 0 || g_opt.drift_tol != 0.0))
+        return fail(KG_EINVAL, "energy recording and drift_tol are not defined for the composed scheme");
     const size_t n3 = (size_t)N * N * N;
     if (!device_ptrs) {
         rc = check_finite(u0, n3, "u0");
@@ -353,8 +366,11 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
         if (e != cudaSuccess) KG_TRY(fail(KG_ECUDA, std::string("copy u0: ") + cudaGetErrorString(e)));
     }
     Tables tb{c->tw, c->tw64, c->coef, c->w2};
-    KG_TRY(init_state(N, c->prec, dt, c->lam, tb, c->phys, v0, device_ptrs, c->S0, c->S1, c->W, fbuf, st));
+    c->scheme = g_scheme;
+    KG_TRY(init_state(N, c->prec, dt, c->lam, tb, c->phys, v0, device_ptrs, c->S0, c->S1, c->W, fbuf, st,
+                      c->scheme == KG_SCHEME_COMPOSED4 ? c->kick : nullptr));
     KgDev d = fresh_dev();
+    d.scheme = c->scheme;
     if (cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "dev upload"));
     {
         cudaError_t e = cudaStreamSynchronize(st);
@@ -379,6 +395,7 @@ int init_common_c(int N, double L, double dt, const double* u0, const double* v0
     int rc = check_grid(N, L, dt);
     if (rc) return rc;
     if (!u0) return fail(KG_EINVAL, "u0 is NULL");
+    if (g_scheme != KG_SCHEME_EQ2) return fail(KG_ENOTSUP, "the composed scheme is built for real fields");
     const size_t n3 = (size_t)N * N * N;
     if (!device_ptrs) {
         rc = check_finite(u0, 2 * n3, "u0");
@@ -459,10 +476,12 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
     KG_CK(col(N, -1, c->W, yps, NX, N, c->tw, st));                               // forward y
     if (timed) KG_CK(cudaEventRecord(c->ev[2], st));
     const bool fused = c->pl->zstep != nullptr;
+    const C4Args c4{c->kick, 3 * (N / 2) * (N / 2) + 1, {c->c4h[0], c->c4h[1], c->c4h[2]}};
+    const C4Args* c4p = c->scheme == KG_SCHEME_COMPOSED4 ? &c4 : nullptr;
     if (fused) {
         // z pass: forward z FFT -> F^n, the update, inverse z FFT, in one kernel
         KG_CK(c->pl->zstep(N, c->cplx, c->W, c->S0, c->S1, c->dev, c->part_sum, c->tw, c->coef, c->w2, 1.0 / c->dt,
-                           st));
+                           c4p, st));
         KG_CK(launch_fin_z(c->part_sum, c->pl->zstep_parts(N, c->cplx), c->part2, c->dev, q_norm, st));
     } else {
         // the IEEE FP64 passes, bound by the FP64 pipe throughout, keep the three kernels
@@ -473,7 +492,8 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
             KG_CK(c->pl->updatec(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, st));
             KG_CK(launch_fin_z(c->part_sum, c->pl->updatec_parts(N), c->part2, c->dev, q_norm, st));
         } else {
-            KG_CK(c->pl->update(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, st));
+            KG_CK(c->pl->update(N, c->W, c->S0, c->S1, c->dev, c->part_sum, c->coef, c->w2, 1.0 / c->dt, c4p,
+                                st));
             KG_CK(launch_fin_z(c->part_sum, c->pl->update_parts(N), c->part2, c->dev, q_norm, st));
         }
         if (timed) KG_CK(cudaEventRecord(c->ev[4], st));
@@ -564,12 +584,16 @@ int kg_init_device(int N, double L, double dt, const double* d_u0, const double*
     return init_common(N, L, dt, d_u0, d_v0, true);
 }
 
+// pipeline passes of one step: one, or three substeps for the composed scheme
+int passes_per_step(const Ctx* c) { return c->scheme == KG_SCHEME_COMPOSED4 ? 3 : 1; }
+
 int kg_step(int n) {
     Ctx* c = g_ctx;
     if (!c) return fail(KG_ESTATE, "kg_step before kg_init");
     if (n < 0) return fail(KG_EINVAL, "n < 0");
     cudaStream_t st = stream_of(c);
-    for (int i = 0; i < n; i++) {
+    const long long passes = (long long)n * passes_per_step(c);
+    for (long long i = 0; i < passes; i++) {
         int rc;
         if (c->launched == 0) {
             rc = launch_step(c, st, false, nullptr);   // first step direct: it also sets kernel attributes
@@ -589,7 +613,8 @@ int kg_step_timed(int n, float* ms) {
     if (n < 0 || !ms) return fail(KG_EINVAL, "bad arguments");
     for (int p = 0; p < 6; p++) ms[p] = 0.f;
     cudaStream_t st = stream_of(c);
-    for (int i = 0; i < n; i++) {
+    const long long passes = (long long)n * passes_per_step(c);
+    for (long long i = 0; i < passes; i++) {
         int rc = launch_step(c, st, true, ms);
         if (rc) return rc;
         c->launched++;
@@ -601,6 +626,7 @@ int kg_energy(double* E) {
     Ctx* c = g_ctx;
     if (!c) return fail(KG_ESTATE, "kg_energy before kg_init");
     if (!E) return fail(KG_EINVAL, "E is NULL");
+    if (c->scheme != KG_SCHEME_EQ2) return fail(KG_ENOTSUP, "the discrete energy is defined for Eq. (2) only");
     const int N = c->N;
     const double h = c->L / N;
     cudaStream_t st = stream_of(c);
@@ -787,6 +813,18 @@ int kg_get_options(kg_options* o) {
     return KG_OK;
 }
 
+int kg_set_scheme(int scheme) {
+    if (scheme != KG_SCHEME_EQ2 && scheme != KG_SCHEME_COMPOSED4) return fail(KG_EINVAL, "unknown scheme");
+    g_scheme = scheme;
+    return KG_OK;
+}
+
+int kg_get_scheme(int* scheme) {
+    if (!scheme) return fail(KG_EINVAL, "scheme is NULL");
+    *scheme = g_scheme;
+    return KG_OK;
+}
+
 int kg_memory(size_t* bytes) {
     if (!bytes) return fail(KG_EINVAL, "NULL");
     *bytes = g_ctx ? g_ctx->bytes : 0;
@@ -841,6 +879,7 @@ int kg_save_state(void* h, size_t cap, size_t* used) {
     hd.have_E0 = c->have_E0 ? 1 : 0;
     hd.E0 = c->E0;
     hd.complex_field = c->cplx ? 1 : 0;
+    hd.scheme = c->scheme;
     hd.payload_bytes = 2 * arr;
     unsigned char* base = (unsigned char*)h;
     cudaStream_t st = stream_of(c);
@@ -867,7 +906,9 @@ int kg_load_state(const void* h, size_t len) {
     if (!(hd.L > 0.0) || !std::isfinite(hd.L) || !(hd.dt > 0.0) || !std::isfinite(hd.dt) ||
         !std::isfinite(hd.nonlinearity) || !std::isfinite(hd.blowup_threshold) || !std::isfinite(hd.drift_tol) ||
         hd.energy_every < 0 || hd.level < 0 || (hd.frozen != 0 && hd.frozen != 1) ||
-        (hd.complex_field != 0 && hd.complex_field != 1))
+        (hd.complex_field != 0 && hd.complex_field != 1) ||
+        (hd.scheme != KG_SCHEME_EQ2 && hd.scheme != KG_SCHEME_COMPOSED4) ||
+        (hd.scheme == KG_SCHEME_COMPOSED4 && (hd.complex_field != 0 || hd.energy_every != 0 || hd.drift_tol != 0.0)))
         return fail(KG_EINVAL, "checkpoint header field out of range");
     const bool cplx = hd.complex_field == 1;
     const size_t nspec = (size_t)hd.N * hd.N * (cplx ? hd.N : hd.N / 2 + 1);
@@ -884,9 +925,11 @@ int kg_load_state(const void* h, size_t len) {
     o.blowup_threshold = hd.blowup_threshold;
     o.drift_tol = hd.drift_tol;
     g_opt = o;
+    g_scheme = hd.scheme;
     Ctx* c = nullptr;
     int rc = create_ctx(hd.N, hd.L, hd.dt, cplx, &c);
     if (rc) return rc;
+    c->scheme = hd.scheme;
     const int N = c->N, NX = cplx ? N : c->NH;
     cudaStream_t st = stream_of(c);
     KgDev d = fresh_dev();
@@ -899,6 +942,7 @@ int kg_load_state(const void* h, size_t len) {
     d.Q_last = hd.Q_last;
     d.Q_last_level = hd.Q_last_level;
     d.complex_field = cplx ? 1 : 0;
+    d.scheme = c->scheme;
     cudaError_t e = cudaMemcpyAsync(c->S0, base + sizeof(hd), arr, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->S1, base + sizeof(hd) + arr, arr, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st);

@@ -436,6 +436,8 @@ struct KgDev {
     double P_peek;            // sum-based P of the last peek
     double maxabs_peek;
     int status;               // nonzero: a device-side check failed
+    int scheme;               // KG_SCHEME_EQ2 (0) or KG_SCHEME_COMPOSED4 (1)
+    int sub;                  // composed scheme: substep 0..2 of the current step
     int pad1;
 };
 

@@ -93,8 +93,34 @@ int make_tables(int N, int prec, double L, double dt, const AllocFn& alloc, Tabl
     return KG_OK;
 }
 
+// composed scheme (triple jump of Eq. (2) in kick-drift-kick form): substep lengths
+// h = (g1, g2, g1) dt, g1 = 1/(2 - 2^{1/3}), g2 = 1 - 2 g1, and per substep s the merged
+// kick K_s = half(h_{s-1}) + half(h_s), half(h) = (h/2)/(1 + omega^2 h^2/4), h_{-1} = h_2
+int make_kick_tables(int N, double L, double dt, const AllocFn& alloc, double2** kick, double h[3]) {
+    const double g1 = 1.0 / (2.0 - std::cbrt(2.0)), g2 = 1.0 - 2.0 * g1;
+    h[0] = g1 * dt;
+    h[1] = g2 * dt;
+    h[2] = g1 * dt;
+    const int m2max = 3 * (N / 2) * (N / 2), stride = m2max + 1;
+    std::vector<double2> t((size_t)3 * stride);
+    const double kf = 2.0 * kPi / L;
+    for (int m2 = 0; m2 <= m2max; m2++) {
+        const double om2 = 1.0 + kf * kf * (double)m2;
+        auto half = [om2](double hs) { return (0.5 * hs) / (1.0 + om2 * hs * hs / 4.0); };
+        for (int s = 0; s < 3; s++) {
+            const double K = half(h[(s + 2) % 3]) + half(h[s]);
+            t[(size_t)s * stride + m2] = make_double2(K, K * om2);
+        }
+    }
+    int rc = alloc((void**)kick, sizeof(double2) * t.size(), "composed-scheme kick tables");
+    if (rc) return rc;
+    KG_HCK(cudaMemcpy(*kick, t.data(), sizeof(double2) * t.size(), cudaMemcpyHostToDevice));
+    return KG_OK;
+}
+
 int init_state(int N, int prec, double dt, double lam, const Tables& tb, double* phys, const double* v0,
-               bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st) {
+               bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st,
+               const double2* kick0) {
     const int NH = N / 2 + 1;
     const size_t nspec = (size_t)N * N * NH, n3 = (size_t)N * N * N;
     const PassLaunch* pl = launcher_for(prec);
@@ -109,7 +135,8 @@ int init_state(int N, int prec, double dt, double lam, const Tables& tb, double*
     } else {
         KG_HCK(cudaMemsetAsync(S1, 0, sizeof(double2) * nspec, st));
     }
-    KG_HCK(launch_startup(N, S0, S1, fbuf, tb.coef, dt, false, st));    // S1 = uh^{-1}
+    if (kick0) KG_HCK(launch_startup_c4(N, S0, S1, fbuf, kick0, st));    // S1 = P^0
+    else KG_HCK(launch_startup(N, S0, S1, fbuf, tb.coef, dt, false, st));  // S1 = uh^{-1}
     KG_HCK(pl->col_from_f64(N, S0, S1, nullptr, W, NH, (size_t)N * NH, N, tb.tw, st));   // z inverse of uh^0
     KG_HCK(pl->col(N, +1, W, (size_t)N * NH, NH, N, tb.tw, st));                          // y inverse
     return KG_OK;

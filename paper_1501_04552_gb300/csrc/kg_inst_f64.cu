@@ -47,6 +47,14 @@ cudaError_t launch_startup(int N, const double2* a, double2* b, const double2* f
     });
 }
 
+cudaError_t launch_startup_c4(int N, const double2* a, double2* b, const double2* f, const double2* kick0,
+                              cudaStream_t st) {
+    KG_DISPATCH_N(N, {
+        k_startup_c4<NN><<<kStrideCtasDeep, 256, 0, st>>>(a, b, f, kick0);
+        return cudaGetLastError();
+    });
+}
+
 cudaError_t launch_energy_q(int N, const double2* x, const double2* y, const double* w2tab, double inv_dt,
                             double* part_sum, int nparts, bool cplx, cudaStream_t st) {
     KG_DISPATCH_N(N, {

@@ -1,6 +1,7 @@
 // kg_kernels.cuh -- kernel templates of the step passes, the set-up and the read-out.
 #pragma once
 #include "kg_fft.cuh"
+#include "kg_launch.h"
 
 namespace kg {
 
@@ -482,6 +483,19 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
 }
 
 // ---------------------------------------------------------------------------
+// Time-stepping schemes of the per-mode update.
+// SCHEME 0, Eq. (2): cur = uh^n, old = uh^{n-1};
+//     uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k   written over old.
+// SCHEME 1, the fourth-order composition (triple jump) of Eq. (2) in kick-drift-kick
+// form: cur = a (= uh), old = P (velocity variable); substep s = dev->sub of a step
+//     P <- P + K_s (F - omega^2 a),   a <- a + h_s P       (both written back)
+// with the merged kick K_s = (h_{s-1}/2)/(1 + omega^2 h_{s-1}^2/4) + (h_s/2)/(1 + omega^2
+// h_s^2/4) (h_{-1} = h_2 = h_0) and h = (g1, g2, g1) dt.  One F per substep; with one
+// substep of length dt this is Eq. (2) itself.
+// ---------------------------------------------------------------------------
+// (the tables and substep lengths travel in C4Args, kg_launch.h)
+
+// ---------------------------------------------------------------------------
 // Streaming update between the forward and the inverse z FFT.  W holds F^n_k on entry
 // and uh^{n+1}_k in the pass precision on exit; the state update and the Q terms are
 // those of z_body.
@@ -574,30 +588,46 @@ __device__ __forceinline__ typename Q::T block_tree_sum(typename Q::T v, typenam
 //     uh^{n+1} = 2 c_k uh^n - uh^{n-1} + 2 beta_k F^n_k        (FP64, over uh^{n-1})
 // and W <- uh^{n+1} in the pass precision for the inverse transforms.  On recording
 // steps each CTA also writes its partial sum of the Q terms (QTerm) times qc = 1/(2 dt^2).
-template <class P, int N, bool CPLX = false>
+template <class P, int N, bool CPLX = false, int SCHEME = 0>
 __global__ void __launch_bounds__(kUpdThreads, 6) k_update(typename P::S* __restrict__ W, double2* S0, double2* S1,
                                                           KgDev* __restrict__ dev, double* __restrict__ part_sum,
                                                           const double2* __restrict__ coef,
-                                                          const double* __restrict__ w2tab, double qr, double qc) {
+                                                          const double* __restrict__ w2tab, double qr, double qc,
+                                                          C4Args c4) {
     typedef typename P::R R;
     typedef QTerm<P> Q;
     typedef ModeIndex<N, CPLX> MI;
     constexpr unsigned kModes = (unsigned)MI::kModes;
     static_assert(MI::kModes < (1ll << 31), "mode indexes fit 32 bits");
     __shared__ typename Q::T red[kUpdThreads / 32];
-    const bool want_q = kg_recording(dev);
+    const bool want_q = SCHEME == 0 && kg_recording(dev);
     const bool update = dev->frozen == 0;
-    const double2* __restrict__ cur = dev->phase ? S1 : S0;
+    double2* __restrict__ cur = dev->phase ? S1 : S0;
     double2* __restrict__ old = dev->phase ? S0 : S1;
     const unsigned i = blockIdx.x * kUpdThreads + threadIdx.x;
     typename Q::T q = Q::zero();
     if (i < kModes) {
         const MI mi((unsigned)i);
         const cx<R> f = P::load(W[i]);
-        const double2 a = cur[i], b = old[i], cf = __ldg(coef + mi.m2);
-        const double nre = P::fma_into(cf.y, f.re, fma(cf.x, a.x, -b.x));
-        const double nim = P::fma_into(cf.y, f.im, fma(cf.x, a.y, -b.y));
-        if (update) old[i] = make_double2(nre, nim);
+        const double2 a = cur[i], b = old[i];
+        double nre, nim;
+        if constexpr (SCHEME == 0) {
+            const double2 cf = __ldg(coef + mi.m2);
+            nre = P::fma_into(cf.y, f.re, fma(cf.x, a.x, -b.x));
+            nim = P::fma_into(cf.y, f.im, fma(cf.x, a.y, -b.y));
+            if (update) old[i] = make_double2(nre, nim);
+        } else {
+            const int sub = dev->sub;
+            const double2 kc = __ldg(c4.kick + (size_t)sub * c4.stride + mi.m2);
+            const double pre = P::fma_into(kc.x, f.re, fma(-kc.y, a.x, b.x));
+            const double pim = P::fma_into(kc.x, f.im, fma(-kc.y, a.y, b.y));
+            nre = fma(c4.h[sub], pre, a.x);
+            nim = fma(c4.h[sub], pim, a.y);
+            if (update) {
+                old[i] = make_double2(pre, pim);
+                cur[i] = make_double2(nre, nim);
+            }
+        }
         W[i] = P::pack(cmake<R>(P::from_f64(nre), P::from_f64(nim)));
         if (want_q) q = Q::term(nre, nim, a, __ldg(w2tab + mi.m2), qr, mi.twice);
     }
@@ -630,11 +660,11 @@ struct ZStepMinBlocks {
     static constexpr int value = kThreads / ZStepShape<N>::NT > 1 ? kThreads / ZStepShape<N>::NT : 1;
 };
 
-template <class P, int N, bool CPLX = false>
+template <class P, int N, bool CPLX = false, int SCHEME = 0>
 __global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value)
     k_zstep(typename P::S* __restrict__ W, double2* S0, double2* S1, KgDev* __restrict__ dev,
             double* __restrict__ part_sum, const typename P::S* __restrict__ tw, const double2* __restrict__ coef,
-            const double* __restrict__ w2tab, double qr, double qc) {
+            const double* __restrict__ w2tab, double qr, double qc, C4Args c4) {
     typedef typename P::R R;
     typedef typename P::S S;
     typedef QTerm<P> Q;
@@ -648,9 +678,9 @@ __global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value
     const bool valid = kx < NX;   // columns of the last tile beyond the plane compute on zeros
     ColSmem<P, C> csm{sm, c};
     tw = stage_table(tw, sm + N * C, N);
-    const bool want_q = kg_recording(dev);
+    const bool want_q = SCHEME == 0 && kg_recording(dev);
     const bool update = dev->frozen == 0;
-    const double2* __restrict__ cur = dev->phase ? S1 : S0;
+    double2* __restrict__ cur = dev->phase ? S1 : S0;
     double2* __restrict__ old = dev->phase ? S0 : S1;
     const size_t rs = (size_t)N * NX, base = (size_t)ky * NX + kx;
 
@@ -678,10 +708,25 @@ __global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value
             const int m2 = mxy2 + mz * mz;
             if (valid) {
                 const size_t idx = base + (size_t)kz * rs;
-                const double2 a = cur[idx], b = old[idx], cf = __ldg(coef + m2);
-                const double nre = P::fma_into(cf.y, v[s].re, fma(cf.x, a.x, -b.x));
-                const double nim = P::fma_into(cf.y, v[s].im, fma(cf.x, a.y, -b.y));
-                if (update) old[idx] = make_double2(nre, nim);
+                const double2 a = cur[idx], b = old[idx];
+                double nre, nim;
+                if constexpr (SCHEME == 0) {
+                    const double2 cf = __ldg(coef + m2);
+                    nre = P::fma_into(cf.y, v[s].re, fma(cf.x, a.x, -b.x));
+                    nim = P::fma_into(cf.y, v[s].im, fma(cf.x, a.y, -b.y));
+                    if (update) old[idx] = make_double2(nre, nim);
+                } else {
+                    const int sub = dev->sub;
+                    const double2 kc = __ldg(c4.kick + (size_t)sub * c4.stride + m2);
+                    const double pre = P::fma_into(kc.x, v[s].re, fma(-kc.y, a.x, b.x));
+                    const double pim = P::fma_into(kc.x, v[s].im, fma(-kc.y, a.y, b.y));
+                    nre = fma(c4.h[sub], pre, a.x);
+                    nim = fma(c4.h[sub], pim, a.y);
+                    if (update) {
+                        old[idx] = make_double2(pre, pim);
+                        cur[idx] = make_double2(nre, nim);
+                    }
+                }
                 if (want_q) q = Q::add(q, Q::term(nre, nim, a, __ldg(w2tab + m2), qr, twice));
                 v[s] = cmake<R>(P::from_f64(nre), P::from_f64(nim));
             }
@@ -736,7 +781,8 @@ __global__ void __launch_bounds__(kFinThreads) k_fin_x(const double* part_sum, c
     double mx;
     fin_reduce(kg_recording(dev) ? part_sum : nullptr, part_max, count, acc, mx);
     if (dev->complex_field) mx = sqrt(mx);   // the keys were |u|^2
-    if (threadIdx.x == 0) {
+    // the composed scheme checks the field at integer times only (its first substep)
+    if (threadIdx.x == 0 && dev->sub == 0) {
         if (!dev->frozen) {
             dev->maxabs_last = mx;
             if (kg_recording(dev)) {
@@ -784,8 +830,13 @@ __global__ void __launch_bounds__(kFinThreads) k_fin_z(const double* part_sum, i
             dev->Q_last = q_norm * acc.value();
             dev->Q_last_level = dev->level;
         }
-        dev->level += 1;
-        dev->phase ^= 1;
+        if (dev->scheme == 0) {
+            dev->level += 1;
+            dev->phase ^= 1;
+        } else {   // composed scheme: the state arrays stay put; a step is three substeps
+            dev->sub = dev->sub == 2 ? 0 : dev->sub + 1;
+            if (dev->sub == 0) dev->level += 1;
+        }
     }
 }
 
@@ -892,6 +943,22 @@ __global__ void k_startup(const double2* __restrict__ a, double2* __restrict__ b
         const double c = 0.5 * cf.x, beta = 0.5 * cf.y;
         const double2 a0 = a[i], v0 = b[i], f0 = f[i];
         b[i] = make_double2(c * a0.x - dt * v0.x + beta * f0.x, c * a0.y - dt * v0.y + beta * f0.y);
+    }
+}
+
+// startup of the composed scheme: b holds vh^0 on entry and the stored velocity variable
+// P^0 = vh^0 - (h_0/2)(F^0 - omega^2 uh^0)/(1 + omega^2 h_0^2/4) on exit (the first
+// merged kick then applies only the opening half kick); kick0 = (K_0, K_0 omega^2) with
+// K_0 = h_0/(1 + omega^2 h_0^2/4)
+template <int N>
+__global__ void k_startup_c4(const double2* __restrict__ a, double2* __restrict__ b, const double2* __restrict__ f,
+                             const double2* __restrict__ kick0) {
+    typedef ModeIndex<N, false> MI;
+    const size_t total = (size_t)MI::kModes;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 kc = kick0[MI((unsigned)i).m2];
+        const double2 a0 = a[i], v0 = b[i], f0 = f[i];
+        b[i] = make_double2(v0.x - 0.5 * (kc.x * f0.x - kc.y * a0.x), v0.y - 0.5 * (kc.x * f0.y - kc.y * a0.y));
     }
 }
 

@@ -16,6 +16,13 @@ constexpr int kStrideCtasDeep = 152 * 8;
 struct KgDev;
 struct EnsParams;
 
+// the composed scheme's per-substep data, passed by value to the update kernels
+struct C4Args {
+    const double2* kick;   // [3][stride]: (K_s, K_s omega^2) by integer m^2
+    int stride;            // entries per substep table (3 (N/2)^2 + 1)
+    double h[3];           // drift length of each substep
+};
+
 // precision ids match KG_FP64 / KG_DF64 / KG_MIXED of kg.h
 struct PassLaunch {
     // x pass over W in the context's precision; mode 0 step, 1 peek.  Writes nparts partials.
@@ -28,9 +35,10 @@ struct PassLaunch {
     cudaError_t (*col_from_f64)(int N, const double2* src0, const double2* src1, const KgDev* dev, void* W,
                                 size_t plane_stride, size_t row_stride, int nplanes, const void* tw, cudaStream_t st);
     // streaming FP64 update between a forward and an inverse z column pass; writes
-    // update_parts(N) Q partials when recording
+    // update_parts(N) Q partials when recording; c4: the composed scheme's tables (NULL:
+    // Eq. (2))
     cudaError_t (*update)(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum, const double2* coef,
-                          const double* w2tab, double inv_dt, cudaStream_t st);
+                          const double* w2tab, double inv_dt, const C4Args* c4, cudaStream_t st);
     int (*update_parts)(int N);
     // one persistent cooperative launch of an ensemble step (kg_ensemble.cuh)
     cudaError_t (*ens_step)(const EnsParams& p, int grid, cudaStream_t st);
@@ -53,7 +61,8 @@ struct PassLaunch {
     // FFT, of a real (cplx = false) or complex field; zstep_parts(N, cplx) Q partials.
     // NULL where the step runs forward z, update and inverse z as three kernels.
     cudaError_t (*zstep)(int N, bool cplx, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum,
-                         const void* tw, const double2* coef, const double* w2tab, double inv_dt, cudaStream_t st);
+                         const void* tw, const double2* coef, const double* w2tab, double inv_dt, const C4Args* c4,
+                         cudaStream_t st);
     int (*zstep_parts)(int N, bool cplx);
 };
 
@@ -70,6 +79,9 @@ int x_inverse_parts(int N);   // partial sums launch_x_inverse writes
 // cplx: full N^3 spectrum of a complex field instead of the half spectrum
 cudaError_t launch_startup(int N, const double2* a, double2* b, const double2* f, const double2* coef, double dt,
                            bool cplx, cudaStream_t st);
+// startup of the composed scheme (real field): b = vh^0 -> P^0 (k_startup_c4)
+cudaError_t launch_startup_c4(int N, const double2* a, double2* b, const double2* f, const double2* kick0,
+                              cudaStream_t st);
 cudaError_t launch_energy_q(int N, const double2* x, const double2* y, const double* w2tab, double inv_dt,
                             double* part_sum, int nparts, bool cplx, cudaStream_t st);
 // complex field, FP64: forward transform along x (u -> out; cube: of lam |u|^2 u) and
@@ -102,12 +114,17 @@ struct Tables {
 };
 typedef std::function<int(void**, size_t, const char*)> AllocFn;
 int make_tables(int N, int prec, double L, double dt, const AllocFn& alloc, Tables* t);
+// the composed scheme's merged-kick tables [3][3 (N/2)^2 + 1] of (K_s, K_s omega^2) and
+// its substep lengths h[3] = (g1, g2, g1) dt
+int make_kick_tables(int N, double L, double dt, const AllocFn& alloc, double2** kick, double h[3]);
 
 // FP64 set-up of one state from the physical field in phys (N^3 doubles, overwritten):
-// S0 = uh^0, S1 = uh^{-1} (startup level), W = yz-inverse of uh^0 in the pass
+// S0 = uh^0, S1 = uh^{-1} (startup level of Eq. (2)) or, with kick0 (the composed
+// scheme's first merged-kick table), S1 = P^0; W = yz-inverse of uh^0 in the pass
 // precision; fbuf is an FP64 spectral scratch (may alias W when W holds 16-byte values)
 int init_state(int N, int prec, double dt, double lam, const Tables& tb, double* phys, const double* v0,
-               bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st);
+               bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st,
+               const double2* kick0 = nullptr);
 
 // the same for a complex field: phys and v0 hold N^3 complex values, S0, S1, W and fbuf
 // the full N^3 spectrum

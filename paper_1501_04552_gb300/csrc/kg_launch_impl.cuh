@@ -131,14 +131,20 @@ struct Launchers {
     static int update_parts(int N) { return (int)(((long long)N * N * (N / 2 + 1) + kUpdThreads - 1) / kUpdThreads); }
     template <int N>
     static cudaError_t update_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
-                                const double* w2, double inv_dt, cudaStream_t st) {
+                                const double* w2, double inv_dt, const C4Args* c4, cudaStream_t st) {
         const double qr = 0.25 / (inv_dt * inv_dt), qc = 0.5 * inv_dt * inv_dt;
-        k_update<P, N><<<update_parts(N), kUpdThreads, 0, st>>>((S*)W, S0, S1, dev, ps, coef, w2, qr, qc);
+        if (c4) {
+            k_update<P, N, false, 1><<<update_parts(N), kUpdThreads, 0, st>>>((S*)W, S0, S1, dev, ps, coef, w2, qr,
+                                                                              qc, *c4);
+        } else {
+            k_update<P, N><<<update_parts(N), kUpdThreads, 0, st>>>((S*)W, S0, S1, dev, ps, coef, w2, qr, qc,
+                                                                   C4Args{});
+        }
         return cudaGetLastError();
     }
     static cudaError_t update(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
-                              const double* w2, double inv_dt, cudaStream_t st) {
-        KG_DISPATCH_N(N, return update_n<NN>(W, S0, S1, dev, ps, coef, w2, inv_dt, st));
+                              const double* w2, double inv_dt, const C4Args* c4, cudaStream_t st) {
+        KG_DISPATCH_N(N, return update_n<NN>(W, S0, S1, dev, ps, coef, w2, inv_dt, c4, st));
     }
     // ---- complex field ----
     template <int N>
@@ -178,31 +184,38 @@ struct Launchers {
         const double qr = 0.25 / (inv_dt * inv_dt), qc = 0.5 * inv_dt * inv_dt;
         KG_DISPATCH_N(N, {
             k_update<P, NN, true><<<updatec_parts(NN), kUpdThreads, 0, st>>>((S*)W, S0, S1, dev, ps, coef, w2, qr,
-                                                                             qc);
+                                                                             qc, C4Args{});
             return cudaGetLastError();
         });
     }
 
     // fused z pass (forward z FFT, update, inverse z FFT) of a real (cplx = false) or
-    // complex field; zstep_parts: the Q partials it writes when recording
-    template <int N, bool CPLX>
+    // complex field, Eq. (2) (SCHEME 0) or the composed scheme (SCHEME 1, real field);
+    // zstep_parts: the Q partials it writes when recording
+    template <int N, bool CPLX, int SCHEME>
     static cudaError_t zstep_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const void* tw,
-                               const double2* coef, const double* w2, double inv_dt, cudaStream_t st) {
+                               const double2* coef, const double* w2, double inv_dt, const C4Args& c4,
+                               cudaStream_t st) {
         typedef ZStepShape<N> Z;
         constexpr int NX = CPLX ? N : N / 2 + 1;
         const size_t smem = (size_t)(N * Z::C + N) * sizeof(S);
-        auto kern = k_zstep<P, N, CPLX>;
+        auto kern = k_zstep<P, N, CPLX, SCHEME>;
         cudaError_t e = set_smem(kern, smem);
         if (e != cudaSuccess) return e;
         const double qr = 0.25 / (inv_dt * inv_dt), qc = 0.5 * inv_dt * inv_dt;
         dim3 grid((NX + Z::C - 1) / Z::C, N);
-        kern<<<grid, Z::NT, smem, st>>>((S*)W, S0, S1, dev, ps, (const S*)tw, coef, w2, qr, qc);
+        kern<<<grid, Z::NT, smem, st>>>((S*)W, S0, S1, dev, ps, (const S*)tw, coef, w2, qr, qc, c4);
         return cudaGetLastError();
     }
     static cudaError_t zstep(int N, bool cplx, void* W, double2* S0, double2* S1, KgDev* dev, double* ps,
-                             const void* tw, const double2* coef, const double* w2, double inv_dt, cudaStream_t st) {
-        if (cplx) { KG_DISPATCH_N(N, return (zstep_n<NN, true>(W, S0, S1, dev, ps, tw, coef, w2, inv_dt, st))); }
-        KG_DISPATCH_N(N, return (zstep_n<NN, false>(W, S0, S1, dev, ps, tw, coef, w2, inv_dt, st)));
+                             const void* tw, const double2* coef, const double* w2, double inv_dt, const C4Args* c4,
+                             cudaStream_t st) {
+        if (cplx) {
+            if (c4) return cudaErrorInvalidValue;   // the composed scheme is built for real fields
+            KG_DISPATCH_N(N, return (zstep_n<NN, true, 0>(W, S0, S1, dev, ps, tw, coef, w2, inv_dt, C4Args{}, st)));
+        }
+        if (c4) { KG_DISPATCH_N(N, return (zstep_n<NN, false, 1>(W, S0, S1, dev, ps, tw, coef, w2, inv_dt, *c4, st))); }
+        KG_DISPATCH_N(N, return (zstep_n<NN, false, 0>(W, S0, S1, dev, ps, tw, coef, w2, inv_dt, C4Args{}, st)));
     }
     static int zstep_parts(int N, bool cplx) {
         const int C = N >= 32 ? ZStepShape<32>::C : ZStepShape<16>::C;

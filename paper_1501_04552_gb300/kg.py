@@ -29,6 +29,10 @@ KG_ESTATE = -8
 KG_FP64 = 0
 KG_DF64 = 1
 KG_MIXED = 2
+
+KG_SCHEME_EQ2 = 0
+KG_SCHEME_COMPOSED4 = 1
+SCHEMES = {"eq2": KG_SCHEME_EQ2, "composed4": KG_SCHEME_COMPOSED4}
 PRECISIONS = {"fp64": KG_FP64, "df64": KG_DF64, "mixed": KG_MIXED}
 
 
@@ -64,6 +68,8 @@ _sig = {
     "kg_set_stream": ([_vp], C.c_int),
     "kg_set_options": ([C.POINTER(kg_options)], C.c_int),
     "kg_get_options": ([C.POINTER(kg_options)], C.c_int),
+    "kg_set_scheme": ([C.c_int], C.c_int),
+    "kg_get_scheme": ([C.POINTER(C.c_int)], C.c_int),
     "kg_status": ([C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_double)],
                   C.c_int),
     "kg_fetch_spectral": ([_vp, _vp], C.c_int),
@@ -229,6 +235,19 @@ def kg_get_options():
     return {f: getattr(o, f) for f, _ in kg_options._fields_}
 
 
+def kg_set_scheme(scheme=KG_SCHEME_EQ2):
+    """time-stepping scheme of the next kg_init: "eq2" (Eq. (2)) or "composed4" (fourth order)"""
+    if isinstance(scheme, str):
+        scheme = SCHEMES[scheme]
+    _check(lib.kg_set_scheme(int(scheme)), "kg_set_scheme")
+
+
+def kg_get_scheme():
+    v = C.c_int()
+    _check(lib.kg_get_scheme(C.byref(v)), "kg_get_scheme")
+    return v.value
+
+
 def kg_status():
     lvl, fr, bl, mx = C.c_longlong(), C.c_int(), C.c_longlong(), C.c_double()
     _check(lib.kg_status(C.byref(lvl), C.byref(fr), C.byref(bl), C.byref(mx)), "kg_status")
@@ -270,7 +289,7 @@ class kg_state_header(C.Structure):
                 ("P_last", C.c_double), ("P_last_level", C.c_longlong), ("Q_last", C.c_double),
                 ("Q_last_level", C.c_longlong), ("have_E0", C.c_int), ("pad0", C.c_int), ("E0", C.c_double),
                 ("payload_bytes", C.c_ulonglong), ("checksum", C.c_ulonglong), ("complex_field", C.c_int),
-                ("pad1", C.c_int), ("reserved", C.c_ubyte * 88)]
+                ("scheme", C.c_int), ("reserved", C.c_ubyte * 88)]
 
 
 STATE_HEADER_BYTES = 256

@@ -65,6 +65,28 @@ def test_options_round_trip_and_validation(kg):
     assert kg.kg_get_options()["precision"] == kg.KG_DF64
 
 
+def test_scheme_round_trip_and_validation(kg):
+    """the scheme applies at the next init; combinations the composed scheme does not
+    define are refused on the host"""
+    kg.lib.kg_finalize()
+    assert kg.kg_get_scheme() == kg.KG_SCHEME_EQ2
+    assert kg.lib.kg_set_scheme(7) == kg.KG_EINVAL
+    assert kg.lib.kg_get_scheme(None) == kg.KG_EINVAL
+    kg.kg_set_scheme("composed4")
+    assert kg.kg_get_scheme() == kg.KG_SCHEME_COMPOSED4
+    u = np.zeros((16, 16, 16))
+    kg.kg_set_options(energy_every=5)
+    assert kg.lib.kg_init(16, 32.0, 0.01, u.ctypes.data, None) == kg.KG_EINVAL
+    assert "composed" in kg.last_error()
+    kg.kg_set_options(drift_tol=1e-6)
+    assert kg.lib.kg_init(16, 32.0, 0.01, u.ctypes.data, None) == kg.KG_EINVAL
+    kg.kg_set_options()
+    uc = np.zeros((16, 16, 16), dtype=np.complex128)
+    assert kg.lib.kg_init_complex(16, 32.0, 0.01, uc.ctypes.data, None) == kg.KG_ENOTSUP
+    kg.kg_set_scheme()
+    assert kg.kg_get_scheme() == kg.KG_SCHEME_EQ2
+
+
 def _rotl_sum(payload):
     """the checkpoint checksum as kg.h defines it: sum mod 2^64 of word i rotated left by i mod 64"""
     w = np.frombuffer(payload.tobytes(), dtype="<u8")
@@ -122,6 +144,8 @@ def test_checkpoint_rejected_on_the_host(kg):
         (dict(level=-3), kg.KG_EINVAL, "range"),
         (dict(frozen=2), kg.KG_EINVAL, "range"),
         (dict(payload_bytes=8), kg.KG_EINVAL, "payload"),
+        (dict(scheme=5), kg.KG_EINVAL, "range"),
+        (dict(scheme=kg.KG_SCHEME_COMPOSED4, energy_every=3), kg.KG_EINVAL, "range"),
     ]
     for over, code, word in cases:
         b = _checkpoint(kg, **over)
