@@ -29,7 +29,7 @@ class Solver:
     """Eq. (2) stepped on the GPU from (u0, v0) on an N^3 grid of side L (N = u0.shape[0])."""
 
     def __init__(self, u0, L, dt, v0=None, precision="df64", energy_every=0, nonlinearity=1.0,
-                 blowup_threshold=0.0, drift_tol=0.0, stream=None):
+                 blowup_threshold=0.0, drift_tol=0.0, stream=None, scheme="eq2"):
         shape = tuple(u0.shape)
         if len(shape) != 3 or len(set(shape)) != 1:
             raise ValueError("u0 must be an N x N x N array")
@@ -39,6 +39,7 @@ class Solver:
             kg.kg_set_stream(stream)
         kg.kg_set_options(precision=precision, energy_every=energy_every, nonlinearity=nonlinearity,
                           blowup_threshold=blowup_threshold, drift_tol=drift_tol)
+        kg.kg_set_scheme(scheme)   # "eq2" (Eq. (2)) or "composed4" (fourth order, real fields)
         if _is_torch_cuda(u0):
             import torch
             u = u0.to(dtype=torch.complex128 if self.complex else torch.float64).contiguous()
@@ -97,7 +98,7 @@ class Solver:
         """a Solver resumed from a checkpoint buffer written by save()"""
         b = buf if isinstance(buf, np.ndarray) else np.frombuffer(buf, dtype=np.uint8)
         h = kg.state_header(b)
-        kg.kg_load_state(b)
+        kg.kg_load_state(b)   # also restores the checkpoint's scheme
         s = cls.__new__(cls)
         s.N, s.L, s.dt = h.N, h.L, h.dt
         s.complex = bool(h.complex_field)

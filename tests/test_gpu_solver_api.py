@@ -73,3 +73,19 @@ def test_save_and_load(mods):
     assert np.array_equal(r.field(), ref)
     r.close()
     kg.kg_set_options()
+
+
+def test_composed_scheme_through_the_object_interface(mods):
+    torch, kg, S = mods
+    N, dt = 32, 0.02
+    u0 = I.gaussian(N, L, 1.1, 2.0)
+    kg.kg_set_scheme("composed4")
+    kg.kg_set_options(precision="df64")
+    kg.kg_init(N, L, dt, u0, None)
+    kg.kg_step(7)
+    ref = kg.kg_fetch(N)
+    with S.Solver(u0, L, dt, precision="df64", scheme="composed4") as s:
+        s.step(7)
+        assert s.level == 7 and np.array_equal(s.field(), ref)
+    kg.kg_set_scheme()
+    kg.kg_set_options()
