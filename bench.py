@@ -95,6 +95,8 @@ KERNEL_NAMES = {"x": "k_pass_x", "z": "k_zstep", "update": "k_update"}
 # FP32 issue peak of the GPU: 152 SMs x 128 FP32 lanes x 2.07 GHz (max SM clock), one
 # instruction per lane per clock
 FP32_ISSUE_PEAK = 152 * 128 * 2.07e9
+# FP64 FMA rate measured on GB300 (2 per SM per clock; profiles/fp_pipes_gb300.md)
+FP64_PEAK = 598e9
 
 
 def df64_fp32_ops(n):
@@ -323,10 +325,18 @@ def main():
     roofline_alu = None
     if prec == "df64" and NG == 512:
         ops = df64_fp32_ops(NG)
-        # the fused z pass: two column transforms (its update runs on the FP64 pipe)
+        # the fused z pass: two column transforms on the FP32 pipe and the update on the FP64
+        # pipe (6 DFMA per mode); frac_pipes adds the two pipes' busy fractions, the share of
+        # the kernel's time their minimum times fill when they do not overlap
         kops = {n: ops["x"] if n == "x" else (2 * ops["col"] if n == "z" else ops["col"]) for n in names}
         per = {n: {"ops": kops[n], "frac": round(kops[n] / (t * 1e-3) / FP32_ISSUE_PEAK, 4)}
                for n, t in zip(names, k_avg) if n != "update"}
+        if "z" in per:
+            t_z = k_avg[names.index("z")] * 1e-3
+            fp64_ops = 6 * NG * NG * (NG // 2 + 1)
+            per["z"]["fp64_ops"] = fp64_ops
+            per["z"]["frac_fp64"] = round(fp64_ops / t_z / FP64_PEAK, 4)
+            per["z"]["frac_pipes"] = round(per["z"]["frac"] + per["z"]["frac_fp64"], 4)
         x_rate = ops["x"] / (k_avg[names.index("x")] * 1e-3)
         roofline_alu = {"bound": "alu", "kernel": "k_pass_x", "achieved": round(x_rate / 1e12, 2),
                         "peak": round(FP32_ISSUE_PEAK / 1e12, 2), "unit": "T FP32 ops/s",

@@ -495,6 +495,33 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
 // ---------------------------------------------------------------------------
 // (the tables and substep lengths travel in C4Args, kg_launch.h)
 
+// The per-mode update of one step (or substep) at mode index idx with integer norm m2, F the
+// transform of the cube there in the pass precision; writes the state (unless frozen) and
+// returns the new uh in FP64, the value the inverse transforms start from.
+template <class P, int SCHEME>
+__device__ __forceinline__ double2 mode_update(cx<typename P::R> f, double2* cur, double2* old, size_t idx, int m2,
+                                               const double2* __restrict__ coef, const C4Args& c4, int sub,
+                                               bool update, double2 a) {
+    const double2 b = old[idx];
+    if constexpr (SCHEME == 0) {
+        const double2 cf = __ldg(coef + m2);
+        const double nre = P::fma_into(cf.y, f.re, fma(cf.x, a.x, -b.x));
+        const double nim = P::fma_into(cf.y, f.im, fma(cf.x, a.y, -b.y));
+        if (update) old[idx] = make_double2(nre, nim);
+        return make_double2(nre, nim);
+    } else {
+        const double2 kc = __ldg(c4.kick + (size_t)sub * c4.stride + m2);
+        const double pre = P::fma_into(kc.x, f.re, fma(-kc.y, a.x, b.x));
+        const double pim = P::fma_into(kc.x, f.im, fma(-kc.y, a.y, b.y));
+        const double2 n = make_double2(fma(c4.h[sub], pre, a.x), fma(c4.h[sub], pim, a.y));
+        if (update) {
+            old[idx] = make_double2(pre, pim);
+            cur[idx] = n;
+        }
+        return n;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Streaming update between the forward and the inverse z FFT.  W holds F^n_k on entry
 // and uh^{n+1}_k in the pass precision on exit; the state update and the Q terms are
@@ -609,27 +636,10 @@ __global__ void __launch_bounds__(kUpdThreads, 6) k_update(typename P::S* __rest
     if (i < kModes) {
         const MI mi((unsigned)i);
         const cx<R> f = P::load(W[i]);
-        const double2 a = cur[i], b = old[i];
-        double nre, nim;
-        if constexpr (SCHEME == 0) {
-            const double2 cf = __ldg(coef + mi.m2);
-            nre = P::fma_into(cf.y, f.re, fma(cf.x, a.x, -b.x));
-            nim = P::fma_into(cf.y, f.im, fma(cf.x, a.y, -b.y));
-            if (update) old[i] = make_double2(nre, nim);
-        } else {
-            const int sub = dev->sub;
-            const double2 kc = __ldg(c4.kick + (size_t)sub * c4.stride + mi.m2);
-            const double pre = P::fma_into(kc.x, f.re, fma(-kc.y, a.x, b.x));
-            const double pim = P::fma_into(kc.x, f.im, fma(-kc.y, a.y, b.y));
-            nre = fma(c4.h[sub], pre, a.x);
-            nim = fma(c4.h[sub], pim, a.y);
-            if (update) {
-                old[i] = make_double2(pre, pim);
-                cur[i] = make_double2(nre, nim);
-            }
-        }
-        W[i] = P::pack(cmake<R>(P::from_f64(nre), P::from_f64(nim)));
-        if (want_q) q = Q::term(nre, nim, a, __ldg(w2tab + mi.m2), qr, mi.twice);
+        const double2 a = cur[i];
+        const double2 n = mode_update<P, SCHEME>(f, cur, old, i, mi.m2, coef, c4, dev->sub, update, a);
+        W[i] = P::pack(cmake<R>(P::from_f64(n.x), P::from_f64(n.y)));
+        if (want_q) q = Q::term(n.x, n.y, a, __ldg(w2tab + mi.m2), qr, mi.twice);
     }
     if (want_q) {
         q = block_tree_sum<Q, kUpdThreads>(q, red);
@@ -701,6 +711,7 @@ __global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value
         const int my = ky <= N / 2 ? ky : ky - N;
         const int mxy2 = mx * mx + my * my;
         const bool twice = !CPLX && kx != 0 && kx != N / 2;
+        const int sub = SCHEME == 0 ? 0 : dev->sub;
 #pragma unroll
         for (int s = 0; s < 8; s++) {
             const int kz = j + T * s;
@@ -708,27 +719,10 @@ __global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value
             const int m2 = mxy2 + mz * mz;
             if (valid) {
                 const size_t idx = base + (size_t)kz * rs;
-                const double2 a = cur[idx], b = old[idx];
-                double nre, nim;
-                if constexpr (SCHEME == 0) {
-                    const double2 cf = __ldg(coef + m2);
-                    nre = P::fma_into(cf.y, v[s].re, fma(cf.x, a.x, -b.x));
-                    nim = P::fma_into(cf.y, v[s].im, fma(cf.x, a.y, -b.y));
-                    if (update) old[idx] = make_double2(nre, nim);
-                } else {
-                    const int sub = dev->sub;
-                    const double2 kc = __ldg(c4.kick + (size_t)sub * c4.stride + m2);
-                    const double pre = P::fma_into(kc.x, v[s].re, fma(-kc.y, a.x, b.x));
-                    const double pim = P::fma_into(kc.x, v[s].im, fma(-kc.y, a.y, b.y));
-                    nre = fma(c4.h[sub], pre, a.x);
-                    nim = fma(c4.h[sub], pim, a.y);
-                    if (update) {
-                        old[idx] = make_double2(pre, pim);
-                        cur[idx] = make_double2(nre, nim);
-                    }
-                }
-                if (want_q) q = Q::add(q, Q::term(nre, nim, a, __ldg(w2tab + m2), qr, twice));
-                v[s] = cmake<R>(P::from_f64(nre), P::from_f64(nim));
+                const double2 a = cur[idx];
+                const double2 n = mode_update<P, SCHEME>(v[s], cur, old, idx, m2, coef, c4, sub, update, a);
+                if (want_q) q = Q::add(q, Q::term(n.x, n.y, a, __ldg(w2tab + m2), qr, twice));
+                v[s] = cmake<R>(P::from_f64(n.x), P::from_f64(n.y));
             }
         }
     }
