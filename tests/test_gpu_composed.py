@@ -162,3 +162,53 @@ def test_eq2_runs_unchanged_after_a_composed_run(kg):
     assert rel(kg.kg_fetch(N), s.fetch()) <= 1e-12
     s.close()
     kg.kg_finalize()
+
+
+def composed_linear_amplitude(w, dt, n):
+    """the exact discrete solution of the composed scheme for one mode of the linear
+    equation: (a, p) after n steps from (1, 0), by products of the 2x2 substep maps"""
+    import math
+    g1 = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+    M = np.eye(2)
+    for h in (g1 * dt, (1.0 - 2.0 * g1) * dt, g1 * dt):
+        g = -w * w / (1.0 + w * w * h * h / 4.0)     # G_h(a) = g a for F = 0
+        kick = np.array([[1.0, 0.0], [0.5 * h * g, 1.0]])
+        drift = np.array([[1.0, h], [0.0, 1.0]])
+        M = kick @ drift @ kick @ M
+    v = np.array([1.0, 0.0])
+    for _ in range(n):
+        v = M @ v
+    assert math.isfinite(v[0])
+    return v[0]
+
+
+@pytest.mark.parametrize("prec", ["df64", "mixed"])
+def test_linear_mode_closed_form_512(kg, prec):
+    """the benchmark's grid size: lam = 0, u0 = cos(k.x), v0 = 0; after n steps the field is
+    a_n cos(k.x) with a_n from the 2x2 substep maps (independent of the oracle)"""
+    import math
+    N, dt, n, m = 512, 0.01, 20, (5, -7, 3)
+    w = math.sqrt(1.0 + sum((2 * math.pi * mi / L) ** 2 for mi in m))
+    u0 = I.plane_wave(N, L, m, "cos")
+    kg.kg_set_scheme("composed4")
+    kg.kg_set_options(precision=prec, nonlinearity=0.0)
+    kg.kg_init(N, L, dt, u0, None)
+    kg.kg_step(n)
+    u = kg.kg_fetch(N)
+    err = np.abs(u - composed_linear_amplitude(w, dt, n) * u0).max()
+    assert err <= (2e-12 if prec == "df64" else 2e-5), (prec, err)
+    kg.kg_finalize()
+    kg.kg_set_scheme()
+    kg.kg_set_options()
+
+
+def test_composed_matches_oracle_128(kg, CO):
+    N, dt, steps = 128, 0.02, 4
+    u0, v0 = ic(N, seed=11)
+    start(kg, "df64", N, dt, u0, v0)
+    kg.kg_step(steps)
+    s = CO.Composed4Solver(N, L, dt, u0, v0)
+    s.step(steps)
+    assert rel(kg.kg_fetch(N), s.field()) <= 1e-12
+    kg.kg_finalize()
+    kg.kg_set_scheme()
