@@ -351,39 +351,23 @@ int init_common(int N, double L, double dt, const double* u0, const double* v0, 
         }                      \
     } while (0)
     cudaStream_t st = stream_of(c);
-    // F^0 = R2C(lam u0^3) goes to W viewed as FP64 when it is large enough, else to a set-up scratch
-    double2* fbuf = nullptr;
-    double2* extra = nullptr;
-    if (c->pl->store_bytes == sizeof(double2)) {
-        fbuf = (double2*)c->W;
-    } else {
-        KG_TRY(dalloc(c, (void**)&extra, sizeof(double2) * c->nspec, "set-up scratch"));
-        fbuf = extra;
-    }
     {
         cudaError_t e = cudaMemcpyAsync(c->phys, u0, sizeof(double) * n3,
                                         device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) KG_TRY(fail(KG_ECUDA, std::string("copy u0: ") + cudaGetErrorString(e)));
     }
+    // the set-up transforms run in the pass precision where it has them (double-float), with
+    // W as their work array; F^0 = R2C(lam u0^3) waits in the FP64 scratch
     Tables tb{c->tw, c->tw64, c->coef, c->w2};
     c->scheme = g_scheme;
-    KG_TRY(init_state(N, c->prec, dt, c->lam, tb, c->phys, v0, device_ptrs, c->S0, c->S1, c->W, fbuf, st,
-                      c->scheme == KG_SCHEME_COMPOSED4 ? c->kick : nullptr));
+    KG_TRY(init_state(N, c->prec, dt, c->lam, tb, c->phys, v0, device_ptrs, c->S0, c->S1, c->W, c->tmp, st,
+                      c->scheme == KG_SCHEME_COMPOSED4 ? c->kick : nullptr, true));
     KgDev d = fresh_dev();
     d.scheme = c->scheme;
     if (cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess) KG_TRY(fail(KG_ECUDA, "dev upload"));
     {
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) KG_TRY(fail(KG_ECUDA, std::string("init: ") + cudaGetErrorString(e)));
-    }
-    if (extra) {
-        cudaFree(extra);
-        for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
-            if (*it == extra) {
-                c->allocs.erase(it);
-                break;
-            }
-        c->bytes -= sizeof(double2) * c->nspec;
     }
 #undef KG_TRY
     g_ctx = c;
@@ -406,27 +390,16 @@ int init_common_c(int N, double L, double dt, const double* u0, const double* v0
     rc = create_ctx(N, L, dt, true, &c);
     if (rc) return rc;
     cudaStream_t st = stream_of(c);
-    double2* fbuf = nullptr;
-    double2* extra = nullptr;
-    if (c->pl->store_bytes == sizeof(double2)) {
-        fbuf = (double2*)c->W;
-    } else {
-        rc = dalloc(c, (void**)&extra, sizeof(double2) * c->nspec, "set-up scratch");
-        if (rc) {
-            destroy(c);
-            return rc;
-        }
-        fbuf = extra;
-    }
     cudaError_t e = cudaMemcpyAsync(c->phys, u0, sizeof(double2) * n3,
                                     device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
         destroy(c);
         return fail(KG_ECUDA, std::string("copy u0: ") + cudaGetErrorString(e));
     }
+    // F^0 = FFT(lam |u0|^2 u0) waits in the FP64 scratch
     Tables tb{c->tw, c->tw64, c->coef, c->w2};
     rc = init_state_c(N, c->prec, dt, c->lam, tb, (double2*)c->phys, (const double2*)v0, device_ptrs, c->S0, c->S1,
-                      c->W, fbuf, st);
+                      c->W, c->tmp, st);
     KgDev d = fresh_dev();
     d.complex_field = 1;
     if (!rc && cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -438,15 +411,6 @@ int init_common_c(int N, double L, double dt, const double* u0, const double* v0
     if (rc) {
         destroy(c);
         return rc;
-    }
-    if (extra) {
-        cudaFree(extra);
-        for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
-            if (*it == extra) {
-                c->allocs.erase(it);
-                break;
-            }
-        c->bytes -= sizeof(double2) * c->nspec;
     }
     g_ctx = c;
     return KG_OK;
@@ -690,6 +654,16 @@ int kg_fetch_device(double* d_u) {
     if (!c) return fail(KG_ESTATE, "kg_fetch before kg_init");
     if (!d_u) return fail(KG_EINVAL, "output pointer is NULL");
     if (c->cplx) return fail(KG_ESTATE, "the context holds a complex field: use kg_fetch_complex");
+    if (c->pl->x_readout) {
+        // read-out in the pass precision (double-float): inverse z and y of uh^n into the FP64
+        // scratch used as a W-format array, then the inverse x into d_u
+        const int N = c->N, NH = c->NH;
+        cudaStream_t st = stream_of(c);
+        KG_CK(c->pl->col_from_f64(N, c->S0, c->S1, c->dev, c->tmp, NH, (size_t)N * NH, N, c->tw, st));
+        KG_CK(c->pl->col(N, +1, c->tmp, (size_t)N * NH, NH, N, c->tw, st));
+        KG_CK(c->pl->x_readout(N, c->tmp, d_u, c->tw, inv_n3(N), st));
+        return KG_OK;
+    }
     int rc = inverse_yz_f64(c, c->S0, c->S1, c->dev);
     if (rc) return rc;
     KG_CK(launch_x_inverse(c->N, c->tmp, d_u, c->tw64, inv_n3(c->N), nullptr, stream_of(c)));

@@ -316,6 +316,12 @@ template <>
 struct Convert<PrecF64, PrecF32> {
     static __device__ __forceinline__ cx<float> go(cx<double> c) { return cmake<float>(d2f_int(c.re), d2f_int(c.im)); }
 };
+template <>
+struct Convert<PrecDF, PrecF64> {   // exact conversions of the two words, one FP64 add each
+    static __device__ __forceinline__ cx<double> go(cx<df> c) {
+        return cmake<double>(f2d_int(c.re.hi) + f2d_int(c.re.lo), f2d_int(c.im.hi) + f2d_int(c.im.lo));
+    }
+};
 
 // ---------------------------------------------------------------------------
 // per-thread statistics of u on the x pass: sum u^4 and max |u|

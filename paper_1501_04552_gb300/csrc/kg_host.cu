@@ -33,6 +33,16 @@ int forward3d_c(int N, const double2* u, double2* out, const double2* tw64, int 
     KG_HCK(kLaunchF64.colc(N, -1, out, N, (size_t)N * N, N, tw64, st));   // z
     return KG_OK;
 }
+// forward 3D transform of a physical FP64 array in the pass precision of pl, W as the
+// work array, into the FP64 spectral array out; cube: of lam u^3 instead of u
+int forward3d_pass(int N, const PassLaunch* pl, const double* u, void* W, double2* out, const void* tw, int cube,
+                   double lam, cudaStream_t st) {
+    const int NH = N / 2 + 1;
+    KG_HCK(pl->x_setup(N, u, W, tw, cube, lam, st));
+    KG_HCK(pl->col(N, -1, W, (size_t)N * NH, NH, N, tw, st));             // y
+    KG_HCK(pl->col_to_f64(N, W, out, NH, (size_t)N * NH, N, tw, st));     // z -> FP64
+    return KG_OK;
+}
 }  // namespace
 
 const PassLaunch* launcher_for(int prec) {
@@ -120,17 +130,22 @@ int make_kick_tables(int N, double L, double dt, const AllocFn& alloc, double2**
 
 int init_state(int N, int prec, double dt, double lam, const Tables& tb, double* phys, const double* v0,
                bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st,
-               const double2* kick0) {
+               const double2* kick0, bool pass_precision) {
     const int NH = N / 2 + 1;
     const size_t nspec = (size_t)N * N * NH, n3 = (size_t)N * N * N;
     const PassLaunch* pl = launcher_for(prec);
     if (!pl) return set_last_error(KG_EINVAL, "unknown precision");
-    int rc = forward3d(N, phys, fbuf, tb.tw64, 1, lam, st);   // F^0 = R2C(lam u0^3)
-    if (!rc) rc = forward3d(N, phys, S0, tb.tw64, 0, lam, st);  // uh^0
+    const bool pass = pass_precision && pl->x_setup != nullptr;
+    auto fwd = [&](double2* out, int cube) {
+        return pass ? forward3d_pass(N, pl, phys, W, out, tb.tw, cube, lam, st)
+                    : forward3d(N, phys, out, tb.tw64, cube, lam, st);
+    };
+    int rc = fwd(fbuf, 1);              // F^0 = R2C(lam u0^3)
+    if (!rc) rc = fwd(S0, 0);           // uh^0
     if (rc) return rc;
     if (v0) {
         KG_HCK(cudaMemcpyAsync(phys, v0, sizeof(double) * n3, v0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        rc = forward3d(N, phys, S1, tb.tw64, 0, lam, st);        // vh^0
+        rc = fwd(S1, 0);                // vh^0
         if (rc) return rc;
     } else {
         KG_HCK(cudaMemsetAsync(S1, 0, sizeof(double2) * nspec, st));

@@ -127,16 +127,15 @@ struct XpShape {
     static_assert(!CTA_SYNC || PPC <= 15, "one named barrier per pair");
 };
 
-template <class P, int N, int MODE, class SM>
-__device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int j, SM& lsm,
-                                            const typename P::S* __restrict__ tw, double scale, typename P::R rlam,
-                                            bool want_sum, Stats<P>& st) {
+// v[s] = X1[k] + i X2[k], k = j + T s, from the half spectra L1, L2 of two x-lines
+// (Hermitian extension; the kx = 0 and N/2 entries contribute their real parts)
+template <class P, int N>
+__device__ __forceinline__ void x_pair_load(const typename P::S* __restrict__ L1, const typename P::S* __restrict__ L2,
+                                            int j, cx<typename P::R> (&v)[8]) {
     typedef typename P::R R;
     typedef cx<R> C;
-    constexpr int NH = N / 2 + 1, T = N / 8;
-    typename P::S* __restrict__ L2 = L1 + NH;
+    constexpr int T = N / 8;
     const R zero = P::from_f64(0.0);
-    C v[8];
 #pragma unroll
     for (int s = 0; s < 8; s++) {
         const int k = j + T * s;
@@ -152,6 +151,48 @@ __device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int 
         }
         v[s] = P::cnorm(cmake<R>(P::rsub(X1.re, X2.im), P::radd(X1.im, X2.re)));   // X1 + i X2
     }
+}
+
+// the half spectra of two real lines from Z = FFT(x1 + i x2) held as v[s] = Z[j + T s]:
+// X1 = (Z + conj Zm) / 2, X2 = -i (Z - conj Zm) / 2, Zm the mirrored entry
+template <class P, int N, class SM>
+__device__ __forceinline__ void x_pair_unpack(typename P::S* __restrict__ L1, typename P::S* __restrict__ L2, int j,
+                                              SM& lsm, const cx<typename P::R> (&v)[8]) {
+    typedef typename P::R R;
+    typedef cx<R> C;
+    constexpr int T = N / 8;
+#pragma unroll
+    for (int s = 0; s < 8; s++) lsm.put(j + T * s, v[s]);
+    lsm.sync();
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+        const int k = j + T * s;
+        if (k <= N / 2) {
+            const C Z = v[s];
+            const C Zm = conj(lsm.get((N - k) & (N - 1)));
+            const C A = P::cadd(Z, Zm), B = P::csub(Z, Zm);      // 2 X1, 2 i X2
+            C x1 = P::cnorm(A), x2 = P::cnorm(cmake<R>(B.im, -B.re));
+            x1.re = P::scale2(x1.re, 0.5);
+            x1.im = P::scale2(x1.im, 0.5);
+            x2.re = P::scale2(x2.re, 0.5);
+            x2.im = P::scale2(x2.im, 0.5);
+            L1[k] = P::pack(x1);
+            L2[k] = P::pack(x2);
+        }
+    }
+    lsm.sync();
+}
+
+template <class P, int N, int MODE, class SM>
+__device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int j, SM& lsm,
+                                            const typename P::S* __restrict__ tw, double scale, typename P::R rlam,
+                                            bool want_sum, Stats<P>& st) {
+    typedef typename P::R R;
+    typedef cx<R> C;
+    constexpr int NH = N / 2 + 1;
+    typename P::S* __restrict__ L2 = L1 + NH;
+    C v[8];
+    x_pair_load<P, N>(L1, L2, j, v);
 #pragma unroll 1
     for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
         fft<P, N>(v, j, tw, 1, lsm, dir == 0 ? +1 : -1);
@@ -172,28 +213,7 @@ __device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int 
             }
         }
     }
-    if (MODE == MODE_STEP) {
-#pragma unroll
-        for (int s = 0; s < 8; s++) lsm.put(j + T * s, v[s]);
-        lsm.sync();
-#pragma unroll
-        for (int s = 0; s < 8; s++) {
-            const int k = j + T * s;
-            if (k <= N / 2) {
-                const C Z = v[s];
-                const C Zm = conj(lsm.get((N - k) & (N - 1)));
-                const C A = P::cadd(Z, Zm), B = P::csub(Z, Zm);      // 2 X1, 2 i X2
-                C x1 = P::cnorm(A), x2 = P::cnorm(cmake<R>(B.im, -B.re));
-                x1.re = P::scale2(x1.re, 0.5);
-                x1.im = P::scale2(x1.im, 0.5);
-                x2.re = P::scale2(x2.re, 0.5);
-                x2.im = P::scale2(x2.im, 0.5);
-                L1[k] = P::pack(x1);
-                L2[k] = P::pack(x2);
-            }
-        }
-        lsm.sync();
-    }
+    if (MODE == MODE_STEP) x_pair_unpack<P, N>(L1, L2, j, lsm, v);
 }
 
 // one element global -> shared without registers (8- or 16-byte values)
@@ -923,6 +943,60 @@ __global__ void __launch_bounds__(kXThreads) k_x_inverse(const double2* __restri
         double mx = 0.0;
         block_reduce<kXThreads>(acc, mx, red);
         if (threadIdx.x == 0) part_sum[blockIdx.x] = acc.value();
+    }
+}
+
+// Set-up and read-out along x in the pass precision, two physical x-lines per N-point
+// complex transform (the pair form of the x pass), one pair per N/8 threads:
+// FWD: physical FP64 lines u_in (lam u^3 when cube) -> their half spectra, unnormalised,
+//      in the pass precision in spec (lines of N/2 + 1);
+// else: half spectra in spec -> physical lines times scale, FP64, into u_out.
+template <class P, int N, bool FWD>
+__global__ void __launch_bounds__(kXThreads) k_x_pair_io(const double* __restrict__ u_in, typename P::S* __restrict__ spec,
+                                                         double* __restrict__ u_out,
+                                                         const typename P::S* __restrict__ tw, int cube, double lam,
+                                                         double scale) {
+    typedef typename P::R R;
+    typedef cx<R> C;
+    typedef XpShape<N> X;
+    constexpr int NH = N / 2 + 1, T = X::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
+    const int pi = threadIdx.x / T, j = threadIdx.x % T;
+    const size_t pair = (size_t)blockIdx.x * X::PPC + pi;
+    LineSmemX<P, X::CTA_SYNC> lsm{sm + pi * X::PADN, 1u + (unsigned)pi, (unsigned)T};
+    typename P::S* __restrict__ L1 = spec + 2 * pair * NH;
+    typename P::S* __restrict__ L2 = L1 + NH;
+    C v[8];
+    if constexpr (FWD) {
+        const double* __restrict__ u1 = u_in + 2 * pair * N;
+        const double* __restrict__ u2 = u1 + N;
+        const R rlam = P::from_f64(lam);
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            const int x = j + T * s;
+            R a = P::from_f64(u1[x]), b = P::from_f64(u2[x]);
+            if (cube) {
+                a = rlam * (a * a * a);
+                b = rlam * (b * b * b);
+            }
+            v[s] = cmake<R>(a, b);
+        }
+        fft<P, N>(v, j, tw, 1, lsm, -1);
+        x_pair_unpack<P, N>(L1, L2, j, lsm, v);
+    } else {
+        x_pair_load<P, N>(L1, L2, j, v);
+        fft<P, N>(v, j, tw, 1, lsm, +1);
+        double* __restrict__ o1 = u_out + 2 * pair * N;
+        double* __restrict__ o2 = o1 + N;
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            const int x = j + T * s;
+            const cx<double> w = Convert<P, PrecF64>::go(
+                cmake<R>(P::scale2(v[s].re, scale), P::scale2(v[s].im, scale)));
+            o1[x] = w.re;
+            o2[x] = w.im;
+        }
     }
 }
 

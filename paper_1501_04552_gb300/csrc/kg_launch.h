@@ -64,6 +64,14 @@ struct PassLaunch {
                          const void* tw, const double2* coef, const double* w2tab, double inv_dt, const C4Args* c4,
                          cudaStream_t st);
     int (*zstep_parts)(int N, bool cplx);
+    // set-up and read-out transforms in the pass precision (NULL: the FP64 kernels serve):
+    // x_setup: physical FP64 lines (lam u^3 when cube) -> half spectra along x in W format;
+    // x_readout: W-format half spectra along x -> physical FP64 lines times scale;
+    // col_to_f64: forward column FFT of a W-format array into an FP64 spectral array
+    cudaError_t (*x_setup)(int N, const double* u, void* spec, const void* tw, int cube, double lam, cudaStream_t st);
+    cudaError_t (*x_readout)(int N, void* spec, double* u, const void* tw, double scale, cudaStream_t st);
+    cudaError_t (*col_to_f64)(int N, const void* W, double2* out, size_t plane_stride, size_t row_stride,
+                              int nplanes, const void* tw, cudaStream_t st);
 };
 
 extern const PassLaunch kLaunchF64;
@@ -118,13 +126,15 @@ int make_tables(int N, int prec, double L, double dt, const AllocFn& alloc, Tabl
 // its substep lengths h[3] = (g1, g2, g1) dt
 int make_kick_tables(int N, double L, double dt, const AllocFn& alloc, double2** kick, double h[3]);
 
-// FP64 set-up of one state from the physical field in phys (N^3 doubles, overwritten):
+// Set-up of one state from the physical field in phys (N^3 doubles, overwritten):
 // S0 = uh^0, S1 = uh^{-1} (startup level of Eq. (2)) or, with kick0 (the composed
 // scheme's first merged-kick table), S1 = P^0; W = yz-inverse of uh^0 in the pass
-// precision; fbuf is an FP64 spectral scratch (may alias W when W holds 16-byte values)
+// precision; fbuf is an FP64 spectral scratch (may alias W when W holds 16-byte values,
+// unless pass_precision).  The transforms run in FP64, or with pass_precision (and a
+// precision that has x_setup) in the pass precision with W as their work array.
 int init_state(int N, int prec, double dt, double lam, const Tables& tb, double* phys, const double* v0,
                bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st,
-               const double2* kick0 = nullptr);
+               const double2* kick0 = nullptr, bool pass_precision = false);
 
 // the same for a complex field: phys and v0 hold N^3 complex values, S0, S1, W and fbuf
 // the full N^3 spectrum

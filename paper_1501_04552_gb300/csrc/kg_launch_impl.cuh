@@ -1,5 +1,6 @@
 // kg_launch_impl.cuh -- template launchers, instantiated once per precision.
 #pragma once
+#include <type_traits>
 #include "kg_complex.cuh"
 #include "kg_ensemble.cuh"
 #include "kg_kernels.cuh"
@@ -126,6 +127,48 @@ struct Launchers {
     static cudaError_t col_from_f64(int N, const double2* src0, const double2* src1, const KgDev* dev, void* W,
                                     size_t pstride, size_t rstride, int nplanes, const void* tw, cudaStream_t st) {
         KG_DISPATCH_N(N, return col_from_f64_n<NN>(src0, src1, dev, W, pstride, rstride, nplanes, tw, st));
+    }
+
+    // set-up and read-out transforms in the pass precision (double-float only: the FP32
+    // passes would degrade the FP64 state, and the FP64 passes have their own kernels)
+    static constexpr bool kPassIO = std::is_same<P, PrecDF>::value;
+    template <int N, bool FWD>
+    static cudaError_t x_io_n(const double* u_in, void* spec, double* u_out, const void* tw, int cube, double lam,
+                              double scale, cudaStream_t st) {
+        typedef XpShape<N> X;
+        const size_t smem = (size_t)X::PPC * X::PADN * sizeof(S);
+        auto kern = k_x_pair_io<P, N, FWD>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<N * N / 2 / X::PPC, kXThreads, smem, st>>>(u_in, (S*)spec, u_out, (const S*)tw, cube, lam, scale);
+        return cudaGetLastError();
+    }
+    static cudaError_t x_setup(int N, const double* u, void* spec, const void* tw, int cube, double lam,
+                               cudaStream_t st) {
+        if constexpr (!kPassIO) return cudaErrorNotSupported;
+        else { KG_DISPATCH_N(N, return (x_io_n<NN, true>(u, spec, nullptr, tw, cube, lam, 1.0, st))); }
+    }
+    static cudaError_t x_readout(int N, void* spec, double* u, const void* tw, double scale, cudaStream_t st) {
+        if constexpr (!kPassIO) return cudaErrorNotSupported;
+        else { KG_DISPATCH_N(N, return (x_io_n<NN, false>(nullptr, spec, u, tw, 0, 0.0, scale, st))); }
+    }
+    // forward column FFT from W (pass precision) into an FP64 spectral array
+    template <int N>
+    static cudaError_t col_to_f64_n(const void* W, double2* out, size_t pstride, size_t rstride, int nplanes,
+                                    const void* tw, cudaStream_t st) {
+        constexpr int C = ColShape<P>::C, NH = N / 2 + 1;
+        const size_t smem = (size_t)(N * C + N) * sizeof(S);
+        auto kern = k_col<P, P, PrecF64, N, -1, NH, C>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((NH + C - 1) / C, nplanes);
+        kern<<<grid, C * N / 8, smem, st>>>((const S*)W, out, pstride, rstride, (const S*)tw);
+        return cudaGetLastError();
+    }
+    static cudaError_t col_to_f64(int N, const void* W, double2* out, size_t pstride, size_t rstride, int nplanes,
+                                  const void* tw, cudaStream_t st) {
+        if constexpr (!kPassIO) return cudaErrorNotSupported;
+        else { KG_DISPATCH_N(N, return (col_to_f64_n<NN>(W, out, pstride, rstride, nplanes, tw, st))); }
     }
 
     static int update_parts(int N) { return (int)(((long long)N * N * (N / 2 + 1) + kUpdThreads - 1) / kUpdThreads); }

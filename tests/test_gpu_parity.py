@@ -82,11 +82,14 @@ def test_initial_state_and_startup_level(kg, oracle, prec):
     N, dt = 32, 0.03
     u0, v0 = smooth_ic(N, 1)
     u = run_gpu(kg, prec, N, dt, u0, v0, 0)
-    assert rel(u, u0) <= 1e-14                      # set-up and read-out are FP64 in every precision
+    # set-up and read-out transforms run in FP64, except for the double-float passes, which
+    # run them in double-float (2^-48 rounding per operation)
+    tol = 5e-14 if prec == "df64" else 1e-14
+    assert rel(u, u0) <= tol
     a, b = kg.kg_fetch_spectral(N)
     ref = oracle.Solver(N, L, dt, u0, v0)
     ra, rb = ref.spectral()
-    assert rel(a, ra) <= 1e-14 and rel(b, rb) <= 1e-14
+    assert rel(a, ra) <= tol and rel(b, rb) <= tol
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -175,6 +178,8 @@ def test_constant_field_golden_levels(kg, prec):
         u = kg.kg_fetch(N)
         eps = 1e-15 if prec != "mixed" else 1e-8
         tol = eps * max(n, 1) * min(max(n, 1), 1 / theta) * amax
+        if prec == "df64":          # set-up and read-out transforms in double-float
+            tol += 1e-14 * amax
         assert np.abs(u - an).max() <= tol, (prec, n, u.flat[0], an)
 
 
