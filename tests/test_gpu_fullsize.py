@@ -106,3 +106,21 @@ def test_200_step_energy_and_precision_split(kg, workload):
     assert np.all(np.abs(e - e[0]) <= 1e-6 * abs(e[0])), np.abs(e - e[0]).max() / abs(e[0])
     assert rel(res["mixed"][0], res["df64"][0]) <= 1e-5
     assert np.abs(res["mixed"][1] - e).max() <= 1e-6 * abs(e[0])
+
+
+def test_double_float_set_up_and_read_out(kg, workload):
+    """the double-float set-up and read-out transforms against the IEEE-FP64 ones at 512^3:
+    the initial state (uh^0, uh^{-1}) and the fetched field agree to double-float rounding"""
+    w = workload
+    kg.kg_set_options(precision="fp64")
+    kg.kg_init(N, L, w["dt"], w["u0"], None)
+    a64, b64 = kg.kg_fetch_spectral(N)
+    u64 = kg.kg_fetch(N)
+    kg.kg_set_options(precision="df64")
+    kg.kg_init(N, L, w["dt"], w["u0"], None)
+    a, b = kg.kg_fetch_spectral(N)
+    assert rel(a, a64) <= 5e-14 and rel(b, b64) <= 5e-14
+    u = kg.kg_fetch(N)
+    assert rel(u, u64) <= 5e-14 and rel(u, w["u0"]) <= 5e-14
+    kg.kg_finalize()
+    kg.kg_set_options()
