@@ -55,8 +55,8 @@ extern "C" {
 #define KG_ESTATE (-8)    /* call out of order (e.g. kg_step before kg_init) */
 
 /* arithmetic of the FFT passes (the state uh, the update and the sums are FP64 in all).
- * The set-up transforms of kg_init and the read-out of kg_fetch run in double-float for
- * KG_DF64 and in IEEE FP64 for the other two. */
+ * The set-up transforms of kg_init / kg_init_complex and the read-out of kg_fetch /
+ * kg_fetch_complex run in double-float for KG_DF64 and in IEEE FP64 for the other two. */
 #define KG_FP64 0   /* IEEE FP64 everywhere */
 #define KG_DF64 1   /* FFT and cube in double-float (pairs of FP32, ~48-bit significand) */
 #define KG_MIXED 2  /* FFT and cube in FP32 (section 1.1.2 scheme, FP32/FP64 split) */

@@ -399,7 +399,7 @@ int init_common_c(int N, double L, double dt, const double* u0, const double* v0
     // F^0 = FFT(lam |u0|^2 u0) waits in the FP64 scratch
     Tables tb{c->tw, c->tw64, c->coef, c->w2};
     rc = init_state_c(N, c->prec, dt, c->lam, tb, (double2*)c->phys, (const double2*)v0, device_ptrs, c->S0, c->S1,
-                      c->W, c->tmp, st);
+                      c->W, c->tmp, st, true);
     KgDev d = fresh_dev();
     d.complex_field = 1;
     if (!rc && cudaMemcpyAsync(c->dev, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -696,6 +696,15 @@ int kg_fetch_complex_device(double* d_u) {
     if (!c) return fail(KG_ESTATE, "kg_fetch_complex before kg_init_complex");
     if (!d_u) return fail(KG_EINVAL, "output pointer is NULL");
     if (!c->cplx) return fail(KG_ESTATE, "the context holds a real field: use kg_fetch");
+    if (c->pl->xc_readout) {
+        // read-out in the pass precision (double-float), as kg_fetch_device
+        const int N = c->N;
+        cudaStream_t st = stream_of(c);
+        KG_CK(c->pl->colc_from_f64(N, c->S0, c->S1, c->dev, c->tmp, N, (size_t)N * N, N, c->tw, st));
+        KG_CK(c->pl->colc(N, +1, c->tmp, (size_t)N * N, N, N, c->tw, st));
+        KG_CK(c->pl->xc_readout(N, c->tmp, (double2*)d_u, c->tw, inv_n3(N), st));
+        return KG_OK;
+    }
     int rc = inverse_yz_f64(c, c->S0, c->S1, c->dev);
     if (rc) return rc;
     KG_CK(launch_xc_inverse(c->N, c->tmp, (double2*)d_u, c->tw64, inv_n3(c->N), nullptr, stream_of(c)));

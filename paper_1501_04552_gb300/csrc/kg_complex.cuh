@@ -98,6 +98,53 @@ __global__ void __launch_bounds__(kXThreads, XcMinBlocks<P>::value) k_pass_xc(ty
     }
 }
 
+// Set-up and read-out along x of a complex field in the pass precision, one line per N/8
+// threads: FWD: complex FP64 lines u_in (lam |u|^2 u when cube) -> their transforms,
+// unnormalised, in spec (pass precision); else spec -> lines times scale, FP64, into u_out.
+template <class P, int N, bool FWD>
+__global__ void __launch_bounds__(kXThreads) k_xc_io(const double2* __restrict__ u_in, typename P::S* __restrict__ spec,
+                                                     double2* __restrict__ u_out,
+                                                     const typename P::S* __restrict__ tw, int cube, double lam,
+                                                     double scale) {
+    typedef typename P::R R;
+    typedef cx<R> C;
+    typedef XcShape<N> X;
+    constexpr int T = X::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename P::S* sm = reinterpret_cast<typename P::S*>(smraw);
+    const int li = threadIdx.x / T, j = threadIdx.x % T;
+    const size_t line = (size_t)blockIdx.x * X::LPC + li;
+    LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN, 1u + (unsigned)li, (unsigned)T};
+    typename P::S* __restrict__ Ls = spec + line * N;
+    C v[8];
+    if constexpr (FWD) {
+        const R rlam = P::from_f64(lam);
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            const double2 z = u_in[line * N + j + T * s];
+            v[s] = Convert<PrecF64, P>::go(cmake<double>(z.x, z.y));
+            if (cube) {
+                const R g = rlam * (v[s].re * v[s].re + v[s].im * v[s].im);
+                v[s].re = g * v[s].re;
+                v[s].im = g * v[s].im;
+            }
+        }
+        fft<P, N>(v, j, tw, 1, lsm, -1);
+#pragma unroll
+        for (int s = 0; s < 8; s++) Ls[j + T * s] = P::pack(v[s]);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 8; s++) v[s] = P::load(Ls[j + T * s]);
+        fft<P, N>(v, j, tw, 1, lsm, +1);
+#pragma unroll
+        for (int s = 0; s < 8; s++) {
+            const cx<double> w = Convert<P, PrecF64>::go(
+                cmake<R>(P::scale2(v[s].re, scale), P::scale2(v[s].im, scale)));
+            u_out[line * N + j + T * s] = make_double2(w.re, w.im);
+        }
+    }
+}
+
 // FP64 set-up: forward transform along x of complex physical lines,
 // out[line][k] = sum_x f(u[line][x]) e^{-2 pi i k x / N}, f(u) = u or lam |u|^2 u
 template <int N>

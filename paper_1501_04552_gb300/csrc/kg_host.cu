@@ -43,6 +43,14 @@ int forward3d_pass(int N, const PassLaunch* pl, const double* u, void* W, double
     KG_HCK(pl->col_to_f64(N, W, out, NH, (size_t)N * NH, N, tw, st));     // z -> FP64
     return KG_OK;
 }
+// the same for a complex physical field (full spectrum)
+int forward3d_c_pass(int N, const PassLaunch* pl, const double2* u, void* W, double2* out, const void* tw, int cube,
+                     double lam, cudaStream_t st) {
+    KG_HCK(pl->xc_setup(N, u, W, tw, cube, lam, st));
+    KG_HCK(pl->colc(N, -1, W, (size_t)N * N, N, N, tw, st));              // y
+    KG_HCK(pl->colc_to_f64(N, W, out, N, (size_t)N * N, N, tw, st));      // z -> FP64
+    return KG_OK;
+}
 }  // namespace
 
 const PassLaunch* launcher_for(int prec) {
@@ -158,16 +166,22 @@ int init_state(int N, int prec, double dt, double lam, const Tables& tb, double*
 }
 
 int init_state_c(int N, int prec, double dt, double lam, const Tables& tb, double2* phys, const double2* v0,
-                 bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st) {
+                 bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st,
+                 bool pass_precision) {
     const size_t n3 = (size_t)N * N * N;
     const PassLaunch* pl = launcher_for(prec);
     if (!pl) return set_last_error(KG_EINVAL, "unknown precision");
-    int rc = forward3d_c(N, phys, fbuf, tb.tw64, 1, lam, st);   // F^0 = FFT(lam |u0|^2 u0)
-    if (!rc) rc = forward3d_c(N, phys, S0, tb.tw64, 0, lam, st);  // uh^0
+    const bool pass = pass_precision && pl->xc_setup != nullptr;
+    auto fwd = [&](double2* out, int cube) {
+        return pass ? forward3d_c_pass(N, pl, phys, W, out, tb.tw, cube, lam, st)
+                    : forward3d_c(N, phys, out, tb.tw64, cube, lam, st);
+    };
+    int rc = fwd(fbuf, 1);              // F^0 = FFT(lam |u0|^2 u0)
+    if (!rc) rc = fwd(S0, 0);           // uh^0
     if (rc) return rc;
     if (v0) {
         KG_HCK(cudaMemcpyAsync(phys, v0, sizeof(double2) * n3, v0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        rc = forward3d_c(N, phys, S1, tb.tw64, 0, lam, st);       // vh^0
+        rc = fwd(S1, 0);                // vh^0
         if (rc) return rc;
     } else {
         KG_HCK(cudaMemsetAsync(S1, 0, sizeof(double2) * n3, st));

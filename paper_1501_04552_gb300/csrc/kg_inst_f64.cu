@@ -8,7 +8,7 @@ const PassLaunch kLaunchF64 = {
     &Launchers<PrecF64>::pass_x, &Launchers<PrecF64>::col, &Launchers<PrecF64>::col_from_f64, &Launchers<PrecF64>::update, &Launchers<PrecF64>::update_parts, &Launchers<PrecF64>::ens_step, &Launchers<PrecF64>::ens_blocks_per_sm, &Launchers<PrecF64>::x_parts, sizeof(PrecF64::S),
     &Launchers<PrecF64>::passc_x, &Launchers<PrecF64>::xc_parts, &Launchers<PrecF64>::colc, &Launchers<PrecF64>::colc_from_f64, &Launchers<PrecF64>::updatec, &Launchers<PrecF64>::updatec_parts,
     nullptr, nullptr,   // no fused z pass: the three-kernel form is faster for FP64
-    nullptr, nullptr, nullptr};
+    nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 }  // namespace kg
 
 namespace kg {

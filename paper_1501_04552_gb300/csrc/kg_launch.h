@@ -72,6 +72,12 @@ struct PassLaunch {
     cudaError_t (*x_readout)(int N, void* spec, double* u, const void* tw, double scale, cudaStream_t st);
     cudaError_t (*col_to_f64)(int N, const void* W, double2* out, size_t plane_stride, size_t row_stride,
                               int nplanes, const void* tw, cudaStream_t st);
+    // the same for a complex field (N-point lines, N columns per plane)
+    cudaError_t (*xc_setup)(int N, const double2* u, void* spec, const void* tw, int cube, double lam,
+                            cudaStream_t st);
+    cudaError_t (*xc_readout)(int N, void* spec, double2* u, const void* tw, double scale, cudaStream_t st);
+    cudaError_t (*colc_to_f64)(int N, const void* W, double2* out, size_t plane_stride, size_t row_stride,
+                               int nplanes, const void* tw, cudaStream_t st);
 };
 
 extern const PassLaunch kLaunchF64;
@@ -139,7 +145,8 @@ int init_state(int N, int prec, double dt, double lam, const Tables& tb, double*
 // the same for a complex field: phys and v0 hold N^3 complex values, S0, S1, W and fbuf
 // the full N^3 spectrum
 int init_state_c(int N, int prec, double dt, double lam, const Tables& tb, double2* phys, const double2* v0,
-                 bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st);
+                 bool v0_on_device, double2* S0, double2* S1, void* W, double2* fbuf, cudaStream_t st,
+                 bool pass_precision = false);
 
 // record a failure for kg_last_error(); returns code
 int set_last_error(int code, const std::string& msg);

@@ -171,6 +171,45 @@ struct Launchers {
         else { KG_DISPATCH_N(N, return (col_to_f64_n<NN>(W, out, pstride, rstride, nplanes, tw, st))); }
     }
 
+    // the same for a complex field (one N-point transform per line, N columns per plane)
+    template <int N, bool FWD>
+    static cudaError_t xc_io_n(const double2* u_in, void* spec, double2* u_out, const void* tw, int cube,
+                               double lam, double scale, cudaStream_t st) {
+        typedef XcShape<N> X;
+        const size_t smem = (size_t)X::LPC * X::PADN * sizeof(S);
+        auto kern = k_xc_io<P, N, FWD>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<N * N / X::LPC, kXThreads, smem, st>>>(u_in, (S*)spec, u_out, (const S*)tw, cube, lam, scale);
+        return cudaGetLastError();
+    }
+    static cudaError_t xc_setup(int N, const double2* u, void* spec, const void* tw, int cube, double lam,
+                                cudaStream_t st) {
+        if constexpr (!kPassIO) return cudaErrorNotSupported;
+        else { KG_DISPATCH_N(N, return (xc_io_n<NN, true>(u, spec, nullptr, tw, cube, lam, 1.0, st))); }
+    }
+    static cudaError_t xc_readout(int N, void* spec, double2* u, const void* tw, double scale, cudaStream_t st) {
+        if constexpr (!kPassIO) return cudaErrorNotSupported;
+        else { KG_DISPATCH_N(N, return (xc_io_n<NN, false>(nullptr, spec, u, tw, 0, 0.0, scale, st))); }
+    }
+    template <int N>
+    static cudaError_t colc_to_f64_n(const void* W, double2* out, size_t pstride, size_t rstride, int nplanes,
+                                     const void* tw, cudaStream_t st) {
+        constexpr int C = ColShape<P>::C;
+        const size_t smem = (size_t)(N * C + N) * sizeof(S);
+        auto kern = k_col<P, P, PrecF64, N, -1, N, C>;
+        cudaError_t e = set_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((N + C - 1) / C, nplanes);
+        kern<<<grid, C * N / 8, smem, st>>>((const S*)W, out, pstride, rstride, (const S*)tw);
+        return cudaGetLastError();
+    }
+    static cudaError_t colc_to_f64(int N, const void* W, double2* out, size_t pstride, size_t rstride, int nplanes,
+                                   const void* tw, cudaStream_t st) {
+        if constexpr (!kPassIO) return cudaErrorNotSupported;
+        else { KG_DISPATCH_N(N, return (colc_to_f64_n<NN>(W, out, pstride, rstride, nplanes, tw, st))); }
+    }
+
     static int update_parts(int N) { return (int)(((long long)N * N * (N / 2 + 1) + kUpdThreads - 1) / kUpdThreads); }
     template <int N>
     static cudaError_t update_n(void* W, double2* S0, double2* S1, KgDev* dev, double* ps, const double2* coef,
