@@ -84,10 +84,9 @@ def kernel_groups(k_ms):
     """names and device ms of a step's kernel groups from kg_step_timed: x, yf, z (the
     fused z pass: forward z FFT, update, inverse z FFT), yi when the update and inverse-z
     slots are empty; else the six separate groups"""
-    from paper_1501_04552_gb300 import kg
     if k_ms[3] == 0.0 and k_ms[4] == 0.0:
         return ["x", "yf", "z", "yi"], [k_ms[0], k_ms[1], k_ms[2], k_ms[5]]
-    return list(kg.STEP_KERNELS), list(k_ms)
+    return ["x", "yf", "zf", "update", "zi", "yi"], list(k_ms)
 
 
 KERNEL_NAMES = {"x": "k_pass_x", "z": "k_zstep", "update": "k_update"}
