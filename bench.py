@@ -318,8 +318,10 @@ def main():
                 "step_achieved": round(step_achieved, 1), "step_frac": round(step_achieved / peak, 4),
                 "kernels": per_kernel}
     if prec == "df64":
-        roofline["limiter"] = ("double-float FFT kernels are FP32-issue-bound (ncu: issue active 76-78 %); "
-                               "their HBM fraction is low by construction, see roofline_alu")
+        roofline["limiter"] = ("arithmetic, not HBM: the double-float transforms are bound by FP32 issue (x and y "
+                               "passes 0.62-0.66 of it, ncu issue active 76-81 %), and the fused z pass adds the "
+                               "FP64 update on the FP64 pipe (frac_pipes of roofline_alu.kernels.z); their HBM "
+                               "fraction is low by construction")
     roofline_alu = None
     if prec == "df64" and NG == 512:
         ops = df64_fp32_ops(NG)
