@@ -114,8 +114,10 @@ int kg_get_options(kg_options* opt);
  * of the step's kernels; adjacent half kicks are merged).  kg_step(n) advances n steps and
  * kg_status reports steps; the blow-up check and the max |u| of kg_status look at the
  * field at integer steps only.  Real fields only (kg_init_complex: KG_ENOTSUP);
- * energy_every and drift_tol must be 0 (kg_init: KG_EINVAL) and kg_energy returns
- * KG_ENOTSUP.  kg_fetch_spectral returns (uh^n, P^n) where the stored velocity variable is
+ * energy_every and drift_tol must be 0 (kg_init: KG_EINVAL).  kg_energy returns the
+ * continuous energy of section 1.1 at step n, evaluated in FP64 with the synchronised
+ * velocity p^n: (h^3/N^3) sum_k w_k (|p^n_k|^2 + omega_k^2 |uh^n_k|^2)/2 - lam (h^3/4) sum u^4
+ * (the composition conserves it to O(dt^4)).  kg_fetch_spectral returns (uh^n, P^n) where the stored velocity variable is
  * P^n = p^n - (g1 dt/2) G_{g1 dt}(uh^n).  The scheme takes effect at the next kg_init (or
  * comes from the checkpoint in kg_load_state). */
 #define KG_SCHEME_EQ2 0

@@ -548,6 +548,28 @@ int kg_init_device(int N, double L, double dt, const double* d_u0, const double*
     return init_common(N, L, dt, d_u0, d_v0, true);
 }
 
+// Energy of the composed scheme at the current (integer) step, in FP64: the continuous
+// functional of section 1.1 with the synchronised velocity p (the stored P plus the
+// pending half kick), E = (h^3/N^3) sum_k w_k (|p|^2 + omega^2 |uh|^2)/2 - lam (h^3/4) sum u^4
+int energy_composed(Ctx* c, double* E) {
+    const int N = c->N;
+    const double h = c->L / N;
+    cudaStream_t st = stream_of(c);
+    int rc = inverse_yz_f64(c, c->S0, c->S1, c->dev);            // phase 0: S0 = uh, S1 = P
+    if (rc) return rc;
+    KG_CK(launch_x_inverse(N, c->tmp, c->phys, c->tw64, inv_n3(N), c->part_sum, st));   // u^n, sum u^4
+    KG_CK(launch_fin_sum(c->part_sum, x_inverse_parts(N), c->lam * h * h * h / 4.0, c->scal + 1, st));
+    rc = forward3d_f64(N, c->phys, c->tmp, c->tw64, 1, c->lam, st);   // F = R2C(lam u^3)
+    if (rc) return rc;
+    KG_CK(launch_energy_c4(N, c->S0, c->S1, c->tmp, c->kick, c->w2, c->part_sum, kStrideCtas, st));
+    KG_CK(launch_fin_sum(c->part_sum, kStrideCtas, h * h * h * inv_n3(N), c->scal, st));
+    double v[2];
+    KG_CK(cudaMemcpyAsync(v, c->scal, sizeof(v), cudaMemcpyDeviceToHost, st));
+    KG_CK(cudaStreamSynchronize(st));
+    *E = v[0] - v[1];
+    return KG_OK;
+}
+
 // pipeline passes of one step: one, or three substeps for the composed scheme
 int passes_per_step(const Ctx* c) { return c->scheme == KG_SCHEME_COMPOSED4 ? 3 : 1; }
 
@@ -590,7 +612,7 @@ int kg_energy(double* E) {
     Ctx* c = g_ctx;
     if (!c) return fail(KG_ESTATE, "kg_energy before kg_init");
     if (!E) return fail(KG_EINVAL, "E is NULL");
-    if (c->scheme != KG_SCHEME_EQ2) return fail(KG_ENOTSUP, "the discrete energy is defined for Eq. (2) only");
+    if (c->scheme == KG_SCHEME_COMPOSED4) return energy_composed(c, E);
     const int N = c->N;
     const double h = c->L / N;
     cudaStream_t st = stream_of(c);

@@ -53,6 +53,10 @@ int forward3d_c_pass(int N, const PassLaunch* pl, const double2* u, void* W, dou
 }
 }  // namespace
 
+int forward3d_f64(int N, const double* u, double2* out, const double2* tw64, int cube, double lam, cudaStream_t st) {
+    return forward3d(N, u, out, tw64, cube, lam, st);
+}
+
 const PassLaunch* launcher_for(int prec) {
     switch (prec) {
         case KG_FP64: return &kLaunchF64;

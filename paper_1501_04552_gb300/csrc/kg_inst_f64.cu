@@ -56,6 +56,40 @@ cudaError_t launch_startup_c4(int N, const double2* a, double2* b, const double2
     });
 }
 
+// Energy of the composed scheme at an integer step, quadratic part: per mode the velocity
+// p = P + (h_0/2) G_{h_0}(uh) = P + (K_0 F - K_0 omega^2 uh) / 2 (kick0 holds (K_0, K_0 omega^2)),
+// and the partial sums of w_k (|p|^2 + omega_k^2 |uh|^2) / 2 (Neumaier, per CTA)
+template <int N>
+__global__ void __launch_bounds__(256) k_energy_c4(const double2* __restrict__ a, const double2* __restrict__ P,
+                                                   const double2* __restrict__ f, const double2* __restrict__ kick0,
+                                                   const double* __restrict__ w2tab, double* __restrict__ part_sum) {
+    typedef ModeIndex<N, false> MI;
+    __shared__ double red[96];
+    const size_t total = (size_t)MI::kModes;
+    NSum acc;
+    acc.s = 0.0;
+    acc.c = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const MI mi((unsigned)i);
+        const double w = mi.twice ? 2.0 : 1.0;
+        const double2 kc = kick0[mi.m2], ai = a[i], pi = P[i], fi = f[i];
+        const double pre = pi.x + 0.5 * (kc.x * fi.x - kc.y * ai.x);
+        const double pim = pi.y + 0.5 * (kc.x * fi.y - kc.y * ai.y);
+        acc.add(w * 0.5 * (pre * pre + pim * pim + w2tab[mi.m2] * (ai.x * ai.x + ai.y * ai.y)));
+    }
+    double mx = 0.0;
+    block_reduce<256>(acc, mx, red);
+    if (threadIdx.x == 0) part_sum[blockIdx.x] = acc.value();
+}
+
+cudaError_t launch_energy_c4(int N, const double2* a, const double2* P, const double2* f, const double2* kick0,
+                             const double* w2tab, double* part_sum, int nparts, cudaStream_t st) {
+    KG_DISPATCH_N(N, {
+        k_energy_c4<NN><<<nparts, 256, 0, st>>>(a, P, f, kick0, w2tab, part_sum);
+        return cudaGetLastError();
+    });
+}
+
 cudaError_t launch_energy_q(int N, const double2* x, const double2* y, const double* w2tab, double inv_dt,
                             double* part_sum, int nparts, bool cplx, cudaStream_t st) {
     KG_DISPATCH_N(N, {

@@ -112,6 +112,12 @@ cudaError_t launch_fin_peek(const double* ps, const double* pm, int count, KgDev
 // stage2, which holds (count + 1023) / 1024 doubles), then the level/phase advance
 cudaError_t launch_fin_z(const double* ps, int count, double* stage2, KgDev* dev, double q_norm, cudaStream_t st);
 cudaError_t launch_fin_sum(const double* ps, int count, double norm, double* out, cudaStream_t st);
+// composed scheme: partials of the quadratic energy sum_k w_k (|p|^2 + omega^2 |a|^2) / 2 with
+// the synchronised velocity p formed from the stored P, F = R2C(lam u^3) and the first kick table
+cudaError_t launch_energy_c4(int N, const double2* a, const double2* P, const double2* f, const double2* kick0,
+                             const double* w2tab, double* part_sum, int nparts, cudaStream_t st);
+// FP64 forward 3D transform of a physical array (cube: of lam u^3 instead of u)
+int forward3d_f64(int N, const double* u, double2* out, const double2* tw64, int cube, double lam, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // shared host helpers (kg_host.cu)

@@ -3,8 +3,6 @@ oracle's composed solver (oracle/composed_oracle.py, plain FP64 with numpy's FFT
 measured order on the GPU, blow-up freezing, checkpoint resume and the calls the scheme
 does not define.  Tolerances as for Eq. (2): relative L2 <= 1e-12 for the FP64 and
 double-float passes, 1e-6 for the FP32 passes."""
-import ctypes
-
 import numpy as np
 import pytest
 
@@ -128,9 +126,8 @@ def test_checkpoint_resume_bit_identical(kg):
     kg.kg_set_scheme()
 
 
-def test_timed_steps_and_undefined_calls(kg):
-    """kg_step_timed runs the same three substeps per step as kg_step; kg_energy is not
-    defined for the composed scheme"""
+def test_timed_steps_match_graph_steps(kg):
+    """kg_step_timed runs the same three substeps per step as kg_step"""
     N = 32
     u0, v0 = ic(N, seed=2)
     start(kg, "mixed", N, 0.02, u0, v0)
@@ -140,8 +137,23 @@ def test_timed_steps_and_undefined_calls(kg):
     ms = kg.kg_step_timed(6)
     assert kg.kg_status()["level"] == 6 and ms[2] > 0.0
     assert np.array_equal(kg.kg_fetch(N), ref)
-    E = ctypes.c_double()
-    assert kg.lib.kg_energy(ctypes.byref(E)) == kg.KG_ENOTSUP
+    kg.kg_finalize()
+    kg.kg_set_scheme()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_energy_matches_oracle(kg, CO, prec):
+    """kg_energy of the composed scheme: the continuous energy with the synchronised velocity,
+    against the oracle's at steps 0, 5 and 15"""
+    N, dt = 32, 0.02
+    u0, v0 = ic(N, seed=6)
+    start(kg, prec, N, dt, u0, v0)
+    s = CO.Composed4Solver(N, L, dt, u0, v0)
+    for n in (0, 5, 15):
+        kg.kg_step(n - kg.kg_status()["level"])
+        s.step(n - s.level)
+        E, Eo = kg.kg_energy(), s.energy()
+        assert abs(E - Eo) <= 10 * TOL[prec] * abs(Eo), (prec, n, E, Eo)
     kg.kg_finalize()
     kg.kg_set_scheme()
 
