@@ -2,6 +2,8 @@
 
 Each translation unit is compiled by its own nvcc process in parallel, then linked
 into paper_1501_04552_gb300/libkg.so.  Object files go to paper_1501_04552_gb300/_build/.
+kg_inst.cu is compiled fifteen times, once per (precision, share) of the pass
+launchers (csrc/kg_inst.h), so that the heavy kernel templates build in parallel.
 """
 import os
 import subprocess
@@ -13,7 +15,12 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkg.so")
-UNITS = ["kg_inst_df.cu", "kg_inst_f64.cu", "kg_inst_f32.cu", "kg_api.cu", "kg_host.cu", "kg_ensemble.cu", "kg_mlp.cu", "kg_noalloc.cu"]
+# (source, extra defines, object name); the double-float shares first: they take longest
+UNITS = ([("kg_inst.cu", ["-DKG_PREC_ID=%d" % p, "-DKG_PART=%d" % s], "kg_inst_p%d_s%d.o" % (p, s))
+          for p in (1, 2, 0) for s in range(5)] +
+         [(f, [], f.replace(".cu", ".o")) for f in
+          ["kg_inst_tables.cu", "kg_common.cu", "kg_api.cu", "kg_host.cu", "kg_ensemble.cu", "kg_mlp.cu",
+           "kg_noalloc.cu"]])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
 
@@ -34,9 +41,11 @@ def build(force=False, verbose=False):
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc] + ARCH + FLAGS + ["-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, defs, name = unit
+        obj = os.path.join(BUILD, name)
+        cmd = [nvcc] + ARCH + FLAGS + defs + ["-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src),
+                                              "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s%s" % (src, r.stdout, r.stderr))
@@ -44,7 +53,7 @@ def build(force=False, verbose=False):
             print(r.stdout + r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(UNITS), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]

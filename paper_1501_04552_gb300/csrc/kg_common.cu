@@ -1,15 +1,8 @@
-// kg_inst_f64.cu -- pass launchers for the PrecF64 precision.
+// kg_common.cu -- kernels every precision shares: the FP64 set-up and read-out
+// transforms, the startup levels, the energy sums outside the recorded steps and the
+// finalisers of a step.
 #define KG_DEFINE_COMMON_KERNELS
 #include "kg_launch_impl.cuh"
-
-namespace kg {
-template struct Launchers<PrecF64>;
-const PassLaunch kLaunchF64 = {
-    &Launchers<PrecF64>::pass_x, &Launchers<PrecF64>::col, &Launchers<PrecF64>::col_from_f64, &Launchers<PrecF64>::update, &Launchers<PrecF64>::update_parts, &Launchers<PrecF64>::ens_step, &Launchers<PrecF64>::ens_blocks_per_sm, &Launchers<PrecF64>::x_parts, sizeof(PrecF64::S),
-    &Launchers<PrecF64>::passc_x, &Launchers<PrecF64>::xc_parts, &Launchers<PrecF64>::colc, &Launchers<PrecF64>::colc_from_f64, &Launchers<PrecF64>::updatec, &Launchers<PrecF64>::updatec_parts,
-    nullptr, nullptr,   // no fused z pass: the three-kernel form is faster for FP64
-    nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-}  // namespace kg
 
 namespace kg {
 
