@@ -202,20 +202,40 @@ def cpu_baseline(workload, sample_steps):
                       % (sample_steps, workload["N"], t1 - t0)}
 
 
+REF_MAX_STEPS = 60      # oracle steps (warm-up + timed) one reference run may take: ~2 s each at 512^3
+
+
 def run_reference(args):
+    """the FP64 oracle as it stands on the host cores: W warm-up steps after its set-up, then
+    K timed steps of the 512^3 workload (K and W as asked, while K + W <= REF_MAX_STEPS)"""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
+    from oracle import oracle as O
     from paper_1501_04552_gb300 import inputs as I
     w = I.bump_noise(N_GRID)
-    sample = max(1, args.steps)
-    base = cpu_baseline(w, sample)     # the oracle's set-up is its warm-up and is not timed
-    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": sample, "warmup": args.warmup, "ms_per_step": 1e3 / base["value"], "higher_is_better": True,
+    steps = max(1, min(args.steps, REF_MAX_STEPS))
+    warmup = max(0, min(args.warmup, REF_MAX_STEPS - steps))
+    t0 = time.perf_counter()
+    s = O.Solver(w["N"], w["L"], w["dt"], w["u0"], w["v0"])
+    t1 = time.perf_counter()
+    s.step(warmup)
+    t2 = time.perf_counter()
+    s.step(steps)
+    t3 = time.perf_counter()
+    s.close()
+    value = steps / (t3 - t2)
+    base = {"value": value, "unit": "steps/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d timed steps of the %d^3 workload after a %.1f s set-up and %d warm-up steps"
+                      % (steps, N_GRID, t1 - t0, warmup)}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "kg512_bump_noise", "N": N_GRID, "L": L_BOX, "dt": DT, "seed": 1501},
             "cpu_baseline": base,
-            "e2e": {"value": base["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if steps != args.steps or warmup != args.warmup:
+        line["capped"] = "steps + warm-up capped at %d oracle steps (about 2 s each)" % REF_MAX_STEPS
     print(json.dumps(line), flush=True)
     return 0
 
@@ -234,13 +254,9 @@ def main():
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid size (512 is the benchmark; smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
-        args.steps = min(args.steps, 3)
         return run_reference(args)
-    args.warmup = max(args.warmup, 3)
-    # energy is recorded on the steps that end at multiples of ENERGY_EVERY; keep the timed
-    # region aligned with that cadence (warm-up and timed steps in whole periods)
-    args.warmup = -(-args.warmup // ENERGY_EVERY) * ENERGY_EVERY
-    args.steps = max(ENERGY_EVERY, -(-args.steps // ENERGY_EVERY) * ENERGY_EVERY)
+    if args.warmup < 3 or args.steps < 1:
+        ap.error("--warmup must be >= 3 and --steps >= 1")
 
     import torch
     rank, world, local = dist_env()
@@ -269,23 +285,29 @@ def main():
             torch.distributed.barrier()
 
     def timed_steps(prec, steps, warmup):
+        """warm-up, then `steps` timed steps with the energy evaluated whenever the level
+        reaches a multiple of ENERGY_EVERY (the workload's cadence, counted from level 0).
+        The warm-up runs the same kernels, an energy evaluation included, so that no kernel
+        is loaded for the first time inside the timed region."""
         kg.kg_set_options(precision=prec, energy_every=ENERGY_EVERY)
         d_u0 = torch.from_numpy(u0).to(f"cuda:{local}")
         kg.kg_init_device(NG, L_BOX, DT, d_u0, None)
         del d_u0
         kg.kg_step(warmup)
+        kg.kg_energy(allow_drift=True)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         energies = []
-        left = steps
-        while left > 0:                       # energy every ENERGY_EVERY levels, as the workload asks
-            k = min(ENERGY_EVERY, left)
+        level, left = warmup, steps
+        while left > 0:
+            k = min(left, ENERGY_EVERY - level % ENERGY_EVERY)
             kg.kg_step(k)
+            level += k
             left -= k
-            if k == ENERGY_EVERY:
+            if level % ENERGY_EVERY == 0:
                 energies.append(kg.kg_energy(allow_drift=True))
         e1.record(stream)
         e1.synchronize()
@@ -414,7 +436,7 @@ def main():
                 # per step: x pass, its finaliser, two forward column passes, update, the
                 # second-stage Q sum, the z finaliser, two inverse column passes; per energy
                 # evaluation: the peek x pass and its finaliser
-                "gpu_launches": STEP_LAUNCHES * args.steps + 2 * (args.steps // ENERGY_EVERY),
+                "gpu_launches": STEP_LAUNCHES * args.steps + 2 * len(energies),
                 "energy_series": {"every": ENERGY_EVERY, "first": energies[0] if energies else None,
                                   "max_rel_drift": (max(abs(e - energies[0]) for e in energies) / abs(energies[0])
                                                     if energies else None)},

@@ -307,8 +307,11 @@ int kg_mlp_finalize(void);
  * which bounds the size: N must be even with N*N*(N/2+1) <= 8192*16384 modes
  * (N <= 644); larger or odd N returns KG_ENOTSUP.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls on a device
- * share the array, so calls that overlap on the GPU (concurrent streams) race.
+ * current, and keeps it for the rest of the process; make that first call before any
+ * stream capture.  A cudaDeviceReset on that device discards the array with the rest
+ * of the device's state, and with it the kept address: do not call this entry point
+ * on a device after resetting it.  All calls on a device share the array, so calls
+ * that overlap on the GPU (concurrent streams) race.
  * Enqueued asynchronously; allocates nothing.  Errors: KG_ENOTSUP, KG_EINVAL
  * (NULL pointer, L or dt not finite and > 0), KG_ECUDA. */
 int kg_energy_q_noalloc(int N, double L, double dt, const double* d_cur, const double* d_old, double* d_Q,

@@ -16,6 +16,7 @@
 // first call made on it.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <string>
 
@@ -35,7 +36,10 @@ constexpr int kMaxDevices = 64;
 // the shared scratch: partial sums of the last call on this device
 __device__ __align__(256) double g_q_scratch[kStaticParts];
 
-double* g_scratch_addr[kMaxDevices] = {nullptr};
+// the array's device address on each device, looked up on the first call made there.
+// Several host threads may make that first call at once: each looks the address up (it is
+// the same on every lookup) and stores it; the slot is atomic so that no read races a write.
+std::atomic<double*> g_scratch_addr[kMaxDevices];
 
 // Q partials: CTA b sums the weighted energy terms of modes [b M, (b+1) M), M = kModesPerPart
 __global__ void __launch_bounds__(kThreads) k_energy_q_parts(const double2* __restrict__ x, const double2* __restrict__ y,
@@ -100,14 +104,13 @@ extern "C" int kg_energy_q_noalloc(int N, double L, double dt, const double* d_c
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(KG_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(KG_ENOTSUP, "kg_energy_q_noalloc: device index too large");
-    if (!g_scratch_addr[dev]) {  // set-up, once per device, with that device current
-        double* p = nullptr;
-        e = cudaGetSymbolAddress((void**)&p, g_q_scratch);
-        if (e != cudaSuccess || !p)
+    double* parts = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!parts) {  // set-up, once per device, with that device current
+        e = cudaGetSymbolAddress((void**)&parts, g_q_scratch);
+        if (e != cudaSuccess || !parts)
             return noalloc_fail(KG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
+        g_scratch_addr[dev].store(parts, std::memory_order_release);
     }
-    double* parts = g_scratch_addr[dev];
     const int nparts = (int)((nmodes + kModesPerPart - 1) / kModesPerPart);
     const double kf = 2.0 * 3.14159265358979323846 / L;
     const double h = L / N;

@@ -53,6 +53,30 @@ def test_noalloc_q_matches_context_energy_twice(kg):
     kg.kg_set_options()
 
 
+def test_noalloc_q_at_512_many_partials(kg):
+    """512^3: 4112 partial sums, so the final sum's threads each add several of them"""
+    import torch
+    N, dt = 512, 0.005
+    kg.kg_set_options(precision="df64", nonlinearity=0.0)
+    kg.kg_init(N, L, dt, I.gaussian(N, L, 1.0, 2.0), 0.2 * I.gaussian(N, L, 1.0, 3.0))
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    for call in range(2):
+        kg.kg_step(3)
+        E = kg.kg_energy()
+        a, b = kg.kg_fetch_spectral(N)
+        d_a = torch.from_numpy(a.view(np.float64)).cuda()
+        d_b = torch.from_numpy(b.view(np.float64)).cuda()
+        del a, b
+        rc = kg.lib.kg_energy_q_noalloc(N, L, dt, d_a.data_ptr(), d_b.data_ptr(), out.data_ptr(), None)
+        assert rc == kg.KG_OK, kg.last_error()
+        torch.cuda.synchronize()
+        q = float(out.item())
+        assert abs(q - E) <= 1e-13 * abs(E), (call, q, E)
+        del d_a, d_b
+    kg.kg_finalize()
+    kg.kg_set_options()
+
+
 def test_noalloc_rejects_sizes_beyond_the_static_scratch(kg):
     import torch
     d = torch.zeros(2, dtype=torch.float64, device="cuda")
