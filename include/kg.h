@@ -125,6 +125,21 @@ int kg_get_options(kg_options* opt);
 int kg_set_scheme(int scheme);   /* KG_EINVAL for an unknown scheme */
 int kg_get_scheme(int* scheme);  /* the scheme the next kg_init uses */
 
+/* ---- xy-plane fusion (FP32 passes) ----
+ * The transforms of a step that mix values within one z-plane only -- the inverse y
+ * transforms that end a step, the x pass (C2R, cube, R2C; section 1.1.2) and the forward
+ * y transforms that begin the next -- run as one kernel in which a cluster of 8 CTAs holds
+ * a whole plane of the FP32 work array in its distributed shared memory, so the plane is
+ * read and written once instead of three times (the paper's section 2.1 counts these
+ * passes over memory as the cost of the FFT).  on = 1 selects it for contexts that can
+ * use it: KG_MIXED, a real field, KG_SCHEME_EQ2, N >= 64; other contexts ignore it.  The
+ * arithmetic is that of the separate passes, so the results are identical to them
+ * (up to the summation order of the recorded sum of u^4).  Takes effect at the next
+ * kg_step; between kg_step calls the state is the same in both forms.  Default 0.
+ * kg_get_xy_fusion: *on as set; *active (may be NULL) = 1 if the current context uses it. */
+int kg_set_xy_fusion(int on);    /* KG_EINVAL unless on is 0 or 1 */
+int kg_get_xy_fusion(int* on, int* active);
+
 /* Current level n, blow-up state (1 if frozen, with the level it froze at) and the
  * max |u| seen by the last step (that of u^{n-1}).  Synchronises. */
 int kg_status(long long* level, int* frozen, long long* blowup_level, double* maxabs);

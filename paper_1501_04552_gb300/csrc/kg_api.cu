@@ -78,12 +78,15 @@ struct Ctx {
     double E0 = 0.0;
     cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaGraphExec_t step_graph = nullptr;   // one captured step, replayed by kg_step
+    cudaGraphExec_t xy_graph = nullptr;     // one captured step of the fused xy form (inverse y included)
     long long launched = 0;                 // steps enqueued so far
+    bool plain_done = false;                // a step of the separate-pass form ran outside a graph
 };
 
 Ctx* g_ctx = nullptr;
 kg_options g_opt = {KG_DF64, 0, 1.0, 0.0, 0.0};
 int g_scheme = KG_SCHEME_EQ2;
+int g_xy_fusion = 0;   // kg_set_xy_fusion
 cudaStream_t g_user_stream = nullptr;
 
 cudaStream_t stream_of(const Ctx* c) { return g_user_stream ? g_user_stream : c->own_stream; }
@@ -115,6 +118,7 @@ void destroy(Ctx* c) {
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
     if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    if (c->xy_graph) cudaGraphExecDestroy(c->xy_graph);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -221,8 +225,11 @@ int reuse_ctx(Ctx* c, double L, double dt, Ctx** out) {
     cudaStream_t st = stream_of(c);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(KG_ECUDA, "reuse: stream sync");
     if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    if (c->xy_graph) cudaGraphExecDestroy(c->xy_graph);
     c->step_graph = nullptr;
+    c->xy_graph = nullptr;
     c->launched = 0;
+    c->plain_done = false;
     const int N = c->N;
     const int m2max = 3 * (N / 2) * (N / 2);
     if (c->tw != (void*)c->tw64) release(c, c->tw, c->pl->store_bytes * N);
@@ -418,8 +425,13 @@ int init_common_c(int N, double L, double dt, const double* u0, const double* v0
 
 // one step; with timed, CUDA events split it into six kernel groups and ms[0..5]
 // accumulate their device times: x pass (+ its finaliser), forward y, forward z, update
-// (+ its finaliser), inverse z, inverse y
-int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
+// (+ its finaliser), inverse z, inverse y.
+// xy = 1 or 2: the fused form (use_xy), whose first kernel runs the x pass and the forward
+// y transforms of every z-plane (after their inverse y transforms when xy = 2, i.e. on
+// every step of a kg_step call but its first); it ends with the z pass and leaves W
+// y-forward, so the caller ends the call with one inverse y pass (xy_close).  Its time
+// goes to the x slot; the forward and inverse y slots stay empty.
+int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms, int xy = 0) {
     const int N = c->N, NH = c->NH;
     const double h = c->L / N;
     const double p_norm = c->lam * h * h * h / 4.0;
@@ -429,7 +441,11 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
     const size_t yps = (size_t)N * NX, zrs = (size_t)N * NX;
     auto col = c->cplx ? c->pl->colc : c->pl->col;
     if (timed) KG_CK(cudaEventRecord(c->ev[0], st));
-    if (c->cplx) {
+    if (xy) {
+        // (inverse y,) x pass, forward y of every z-plane in one cluster launch
+        KG_CK(c->pl->xy_fused(N, xy == 2, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
+        KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->xy_parts(N), c->dev, p_norm, st));
+    } else if (c->cplx) {
         KG_CK(c->pl->passc_x(N, MODE_STEP, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
         KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->xc_parts(N), c->dev, p_norm, st));
     } else {
@@ -437,7 +453,7 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
         KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->x_parts(N), c->dev, p_norm, st));
     }
     if (timed) KG_CK(cudaEventRecord(c->ev[1], st));
-    KG_CK(col(N, -1, c->W, yps, NX, N, c->tw, st));                               // forward y
+    if (!xy) KG_CK(col(N, -1, c->W, yps, NX, N, c->tw, st));                      // forward y
     if (timed) KG_CK(cudaEventRecord(c->ev[2], st));
     const bool fused = c->pl->zstep != nullptr;
     const C4Args c4{c->kick, 3 * (N / 2) * (N / 2) + 1, {c->c4h[0], c->c4h[1], c->c4h[2]}};
@@ -464,7 +480,7 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms) {
         KG_CK(col(N, +1, c->W, NX, zrs, N, c->tw, st));                           // inverse z
     }
     if (timed) KG_CK(cudaEventRecord(c->ev[5], st));
-    KG_CK(col(N, +1, c->W, yps, NX, N, c->tw, st));                               // inverse y
+    if (!xy) KG_CK(col(N, +1, c->W, yps, NX, N, c->tw, st));                      // inverse y
     if (timed) {
         KG_CK(cudaEventRecord(c->ev[6], st));
         KG_CK(cudaEventSynchronize(c->ev[6]));
@@ -498,6 +514,45 @@ int ensure_step_graph(Ctx* c, cudaStream_t st) {
     e = cudaGraphInstantiate(&c->step_graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(KG_ECUDA, std::string("step graph instantiate: ") + cudaGetErrorString(e));
+    return KG_OK;
+}
+
+// the fused xy form serves the FP32 passes of a real field under Eq. (2) from N = 64 on,
+// when kg_set_xy_fusion asked for it
+bool use_xy(const Ctx* c) {
+    return g_xy_fusion && c->pl->xy_fused && c->pl->xy_parts && !c->cplx && c->scheme == KG_SCHEME_EQ2 && c->N >= 64 &&
+           c->pl->xy_parts(c->N) > 0;
+}
+
+// the inverse y pass that ends a kg_step call of the fused form (W back to the y-inverse)
+int xy_close(Ctx* c, cudaStream_t st, bool timed, float* ms) {
+    const int N = c->N, NX = c->NH;
+    if (timed) KG_CK(cudaEventRecord(c->ev[5], st));
+    KG_CK(c->pl->col(N, +1, c->W, (size_t)N * NX, NX, N, c->tw, st));
+    if (timed) {
+        KG_CK(cudaEventRecord(c->ev[6], st));
+        KG_CK(cudaEventSynchronize(c->ev[6]));
+        float t = 0.f;
+        KG_CK(cudaEventElapsedTime(&t, c->ev[5], c->ev[6]));
+        ms[5] += t;
+    }
+    return KG_OK;
+}
+
+// capture one step of the fused form with its inverse y transforms
+int ensure_xy_graph(Ctx* c, cudaStream_t st) {
+    if (c->xy_graph) return KG_OK;
+    cudaGraph_t g = nullptr;
+    KG_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_step(c, st, false, nullptr, 2);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : fail(KG_ECUDA, std::string("xy step graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&c->xy_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(KG_ECUDA, std::string("xy step graph instantiate: ") + cudaGetErrorString(e));
     return KG_OK;
 }
 
@@ -579,10 +634,27 @@ int kg_step(int n) {
     if (n < 0) return fail(KG_EINVAL, "n < 0");
     cudaStream_t st = stream_of(c);
     const long long passes = (long long)n * passes_per_step(c);
+    if (use_xy(c) && passes > 0) {
+        // first step without the inverse y transforms (W holds the y-inverse between
+        // calls), the others from the captured fused step, then one inverse y pass
+        for (long long i = 0; i < passes; i++) {
+            int rc;
+            if (i == 0) {
+                rc = launch_step(c, st, false, nullptr, 1);
+            } else {
+                rc = ensure_xy_graph(c, st);
+                if (!rc && cudaGraphLaunch(c->xy_graph, st) != cudaSuccess) rc = fail(KG_ECUDA, "cudaGraphLaunch(xy)");
+            }
+            if (rc) return rc;
+            c->launched++;
+        }
+        return xy_close(c, st, false, nullptr);
+    }
     for (long long i = 0; i < passes; i++) {
         int rc;
-        if (c->launched == 0) {
+        if (!c->plain_done) {
             rc = launch_step(c, st, false, nullptr);   // first step direct: it also sets kernel attributes
+            c->plain_done = true;
         } else {
             rc = ensure_step_graph(c, st);
             if (!rc && cudaGraphLaunch(c->step_graph, st) != cudaSuccess) rc = fail(KG_ECUDA, "cudaGraphLaunch(step)");
@@ -600,11 +672,13 @@ int kg_step_timed(int n, float* ms) {
     for (int p = 0; p < 6; p++) ms[p] = 0.f;
     cudaStream_t st = stream_of(c);
     const long long passes = (long long)n * passes_per_step(c);
+    const bool xy = use_xy(c);
     for (long long i = 0; i < passes; i++) {
-        int rc = launch_step(c, st, true, ms);
+        int rc = launch_step(c, st, true, ms, xy ? (i == 0 ? 1 : 2) : 0);
         if (rc) return rc;
         c->launched++;
     }
+    if (xy && passes > 0) return xy_close(c, st, true, ms);
     return KG_OK;
 }
 
@@ -821,6 +895,24 @@ int kg_get_options(kg_options* o) {
 int kg_set_scheme(int scheme) {
     if (scheme != KG_SCHEME_EQ2 && scheme != KG_SCHEME_COMPOSED4) return fail(KG_EINVAL, "unknown scheme");
     g_scheme = scheme;
+    return KG_OK;
+}
+
+int kg_set_xy_fusion(int on) {
+    if (on != 0 && on != 1) return fail(KG_EINVAL, "kg_set_xy_fusion: on must be 0 or 1");
+    if (g_ctx && g_xy_fusion != on) {
+        // the next kg_step takes the other form; W holds the y-inverse between calls in both
+        cudaStream_t st = stream_of(g_ctx);
+        KG_CK(cudaStreamSynchronize(st));
+    }
+    g_xy_fusion = on;
+    return KG_OK;
+}
+
+int kg_get_xy_fusion(int* on, int* active) {
+    if (!on) return fail(KG_EINVAL, "kg_get_xy_fusion: NULL");
+    *on = g_xy_fusion;
+    if (active) *active = (g_ctx && use_xy(g_ctx)) ? 1 : 0;
     return KG_OK;
 }
 

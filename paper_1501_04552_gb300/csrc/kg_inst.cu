@@ -35,6 +35,11 @@ cudaError_t x_setup(int N, const double* u, void* spec, const void* tw, int cube
 cudaError_t x_readout(int N, void* spec, double* u, const void* tw, double scale, cudaStream_t st) {
     return Lp::x_readout(N, spec, u, tw, scale, st);
 }
+cudaError_t xy_fused(int N, int do_yi, void* W, KgDev* dev, double* ps, double* pm, const void* tw, double scale,
+                     double lam, cudaStream_t st) {
+    return Lp::xy_fused(N, do_yi, W, dev, ps, pm, tw, scale, lam, st);
+}
+int xy_parts(int N) { return Lp::xy_parts(N); }
 #elif KG_PART == 1
 cudaError_t col(int N, int sign, void* W, size_t ps, size_t rs, int nplanes, const void* tw, cudaStream_t st) {
     return Lp::col(N, sign, W, ps, rs, nplanes, tw, st);

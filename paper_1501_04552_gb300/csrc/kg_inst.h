@@ -19,6 +19,8 @@
     KG_INST_FN(x_parts) x_parts;                                                       \
     KG_INST_FN(x_setup) x_setup;                                                       \
     KG_INST_FN(x_readout) x_readout;                                                   \
+    KG_INST_FN(xy_fused) xy_fused;                                                     \
+    KG_INST_FN(xy_parts) xy_parts;                                                     \
     KG_INST_FN(col) col;                      /* share 1: column passes */             \
     KG_INST_FN(col_from_f64) col_from_f64;                                             \
     KG_INST_FN(col_to_f64) col_to_f64;                                                 \

@@ -21,8 +21,10 @@ struct XShape {
     static_assert(T <= 32, "one line must fit in a warp");
 };
 
-template <class P, int N>
-__device__ __forceinline__ void x_load_c2r(const typename P::S* line, int j, const typename P::S* __restrict__ tw,
+// LIN: a pointer to the line's N/2+1 values, or any type whose operator[] yields them
+// (the cluster-fused pass reads lines spread over the shared memory of several CTAs)
+template <class P, int N, class LIN = const typename P::S*>
+__device__ __forceinline__ void x_load_c2r(LIN line, int j, const typename P::S* __restrict__ tw,
                                            cx<typename P::R> (&v)[8]) {
     typedef typename P::R R;
     typedef cx<R> C;
@@ -48,16 +50,17 @@ __device__ __forceinline__ void x_load_c2r(const typename P::S* line, int j, con
 
 // One x-line (T = N/16 threads, thread j): C2R, scale, stats, and in MODE_STEP the
 // cube, R2C and write-back.  The line is read from Lin (global memory, or the line's
-// landing slot in shared memory, which may be lsm's own storage) and written to L.
-template <class P, int N, int MODE>
-__device__ __forceinline__ void x_line_body(const typename P::S* Lin, typename P::S* __restrict__ L, int j,
+// landing slot in shared memory, which may be lsm's own storage) and written to L
+// (pointers, or element accessors as for x_load_c2r; every read precedes every write).
+template <class P, int N, int MODE, class LIN = const typename P::S*, class LOUT = typename P::S* __restrict__>
+__device__ __forceinline__ void x_line_body(LIN Lin, LOUT L, int j,
                                             LineSmem<P>& lsm, const typename P::S* __restrict__ tw, double scale,
                                             typename P::R rlam, bool want_sum, Stats<P>& st) {
     typedef typename P::R R;
     typedef cx<R> C;
     constexpr int M = N / 2, T = XShape<N>::T;
     C v[8];
-    x_load_c2r<P, N>(Lin, j, tw, v);
+    x_load_c2r<P, N, LIN>(Lin, j, tw, v);
     lsm.sync();   // every lane has read Lin before the first exchange writes lsm
     // inverse transform, then (stepping pass) the forward one, through one copy of the code
 #pragma unroll 1
@@ -682,11 +685,12 @@ struct ZStepShape {
     static constexpr int C = N >= 32 ? 8 : 16;
     static constexpr int NT = C * N / 8;
 };
-// resident threads per SM the kernel is compiled for: 1024 (64 registers; the
-// double-float body spills a little there and is still faster than at 512 threads)
+// resident threads per SM the kernel is compiled for: 1024 (64 registers); 1536 for the
+// FP32 passes at N = 512, whose smaller body fits 40 registers and gains from the extra
+// loads in flight (1.046 -> 1.005 ms; not measured at other sizes, which keep 1024)
 template <class P, int N>
 struct ZStepMinBlocks {
-    static constexpr int kThreads = 1024;
+    static constexpr int kThreads = (sizeof(typename P::S) == 8 && N >= 512) ? 1536 : 1024;
     static constexpr int value = kThreads / ZStepShape<N>::NT > 1 ? kThreads / ZStepShape<N>::NT : 1;
 };
 
@@ -708,10 +712,6 @@ __global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value
     const bool valid = kx < NX;   // columns of the last tile beyond the plane compute on zeros
     ColSmem<P, C> csm{sm, c};
     tw = stage_table(tw, sm + N * C, N);
-    const bool want_q = SCHEME == 0 && kg_recording(dev);
-    const bool update = dev->frozen == 0;
-    double2* __restrict__ cur = dev->phase ? S1 : S0;
-    double2* __restrict__ old = dev->phase ? S0 : S1;
     const size_t rs = (size_t)N * NX, base = (size_t)ky * NX + kx;
 
     cx<R> v[8];
@@ -727,6 +727,13 @@ __global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value
     for (int dir = 0; dir < 2; dir++) {
         fft<P, N>(v, j, tw, 1, csm, dir == 0 ? -1 : +1);
         if (dir == 1) break;
+        // the run state is read only now, so that nothing of it is live across the
+        // forward transform (at 64 registers: 132 -> 8 bytes of spills, 1.98 -> 1.91 ms
+        // for the double-float pass at 512^3)
+        const bool want_q = SCHEME == 0 && kg_recording(dev);
+        const bool update = dev->frozen == 0;
+        double2* __restrict__ cur = dev->phase ? S1 : S0;
+        double2* __restrict__ old = dev->phase ? S0 : S1;
         const int mx = (CPLX && kx > N / 2) ? kx - N : kx;
         const int my = ky <= N / 2 ? ky : ky - N;
         const int mxy2 = mx * mx + my * my;
@@ -750,7 +757,7 @@ __global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value
 #pragma unroll
         for (int s = 0; s < 8; s++) W[base + (size_t)(j + T * s) * rs] = P::pack(v[s]);
     }
-    if (want_q) {
+    if (SCHEME == 0 && kg_recording(dev)) {
         q = block_tree_sum<Q, NT>(q, red);
         if (threadIdx.x == 0) part_sum[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = qc * Q::value(q);
     }

@@ -78,6 +78,13 @@ struct PassLaunch {
     cudaError_t (*xc_readout)(int N, void* spec, double2* u, const void* tw, double scale, cudaStream_t st);
     cudaError_t (*colc_to_f64)(int N, const void* W, double2* out, size_t plane_stride, size_t row_stride,
                                int nplanes, const void* tw, cudaStream_t st);
+    // inverse y, x pass and forward y of every z-plane in one launch of thread-block
+    // clusters (kg_xyfuse.cuh; NULL where not built): do_yi = 0 leaves out the inverse y
+    // transforms (W already holds the y-inverse); writes xy_parts(N) partials of the x
+    // pass's statistics; cudaErrorNotSupported for grids it is not built for
+    cudaError_t (*xy_fused)(int N, int do_yi, void* W, KgDev* dev, double* part_sum, double* part_max,
+                            const void* tw, double scale, double lam, cudaStream_t st);
+    int (*xy_parts)(int N);
 };
 
 extern const PassLaunch kLaunchF64;

@@ -5,8 +5,13 @@
 #include "kg_ensemble.cuh"
 #include "kg_kernels.cuh"
 #include "kg_launch.h"
+#include "kg_xyfuse.cuh"
 
 namespace kg {
+
+// CTAs per cluster of the fused xy pass: a plane of FP32 W is 1.05 MB at N = 512, which
+// eight CTAs hold in 136 KB of shared memory each
+constexpr int kXyCluster = 8;
 
 // dynamic shared memory limit of a kernel (static shared memory comes on top, so the
 // attribute is set whatever the size)
@@ -303,6 +308,88 @@ struct Launchers {
         const int C = N >= 32 ? ZStepShape<32>::C : ZStepShape<16>::C;
         const int nx = cplx ? N : N / 2 + 1;
         return (nx + C - 1) / C * N;
+    }
+
+    // ---- fused inverse y / x / forward y pass (FP32 work array, real field) ----
+    template <int N, bool DO_YI>
+    static cudaLaunchConfig_t xy_config(cudaLaunchAttribute* attr, int grid, cudaStream_t st) {
+        typedef XyShape<N, kXyCluster> X;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(X::NT);
+        cfg.dynamicSmemBytes = (size_t)(X::SLAB + X::XBUF) * sizeof(float2);
+        cfg.stream = st;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kXyCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cfg;
+    }
+    // persistent grid: as many clusters as fit on the device at once, at most one per
+    // plane; cached per grid size (both variants share it)
+    template <int N>
+    static int xy_grid_n() {
+        static int grid = 0;
+        if (grid == 0) {
+            cudaLaunchAttribute attr[1];
+            cudaLaunchConfig_t cfg = xy_config<N, true>(attr, kXyCluster, nullptr);
+            int nc0 = 0, nc1 = 0;
+            if (set_smem(k_xy_cluster<N, kXyCluster, true>, cfg.dynamicSmemBytes) != cudaSuccess ||
+                set_smem(k_xy_cluster<N, kXyCluster, false>, cfg.dynamicSmemBytes) != cudaSuccess ||
+                cudaOccupancyMaxActiveClusters(&nc0, k_xy_cluster<N, kXyCluster, true>, &cfg) != cudaSuccess ||
+                cudaOccupancyMaxActiveClusters(&nc1, k_xy_cluster<N, kXyCluster, false>, &cfg) != cudaSuccess)
+                return 0;
+            int nc = nc0 < nc1 ? nc0 : nc1;
+            nc = nc < N ? nc : N;
+            grid = nc * kXyCluster;
+        }
+        return grid;
+    }
+    template <int N, bool DO_YI>
+    static cudaError_t xy_n(void* W, KgDev* dev, double* ps, double* pm, const void* tw, double scale, double lam,
+                            cudaStream_t st) {
+        const int grid = xy_grid_n<N>();
+        if (grid < kXyCluster) return cudaErrorInvalidConfiguration;
+        auto kern = k_xy_cluster<N, kXyCluster, DO_YI>;
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = xy_config<N, DO_YI>(attr, grid, st);
+        cudaError_t e = set_smem(kern, cfg.dynamicSmemBytes);
+        if (e != cudaSuccess) return e;
+        return cudaLaunchKernelEx(&cfg, kern, (float2*)W, dev, ps, pm, (const float2*)tw, scale, lam);
+    }
+    static cudaError_t xy_fused(int N, int do_yi, void* W, KgDev* dev, double* ps, double* pm, const void* tw,
+                                double scale, double lam, cudaStream_t st) {
+        if constexpr (!std::is_same<P, PrecF32>::value) {
+            return cudaErrorNotSupported;
+        } else {
+#define KG_XY_CASE(NN)                                                                       \
+    case NN:                                                                                 \
+        return do_yi ? xy_n<NN, true>(W, dev, ps, pm, tw, scale, lam, st)                    \
+                     : xy_n<NN, false>(W, dev, ps, pm, tw, scale, lam, st);
+            switch (N) {
+                KG_XY_CASE(64)
+                KG_XY_CASE(128)
+                KG_XY_CASE(256)
+                KG_XY_CASE(512)
+                default: return cudaErrorNotSupported;
+            }
+#undef KG_XY_CASE
+        }
+    }
+    static int xy_parts(int N) {
+        if constexpr (!std::is_same<P, PrecF32>::value) {
+            return 0;
+        } else {
+            switch (N) {
+                case 64: return xy_grid_n<64>();
+                case 128: return xy_grid_n<128>();
+                case 256: return xy_grid_n<256>();
+                case 512: return xy_grid_n<512>();
+                default: return 0;
+            }
+        }
     }
 
     static size_t ens_smem() {

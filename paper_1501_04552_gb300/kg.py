@@ -70,6 +70,8 @@ _sig = {
     "kg_get_options": ([C.POINTER(kg_options)], C.c_int),
     "kg_set_scheme": ([C.c_int], C.c_int),
     "kg_get_scheme": ([C.POINTER(C.c_int)], C.c_int),
+    "kg_set_xy_fusion": ([C.c_int], C.c_int),
+    "kg_get_xy_fusion": ([C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "kg_status": ([C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_double)],
                   C.c_int),
     "kg_fetch_spectral": ([_vp, _vp], C.c_int),
@@ -246,6 +248,18 @@ def kg_get_scheme():
     v = C.c_int()
     _check(lib.kg_get_scheme(C.byref(v)), "kg_get_scheme")
     return v.value
+
+
+def kg_set_xy_fusion(on=True):
+    """the cluster-fused inverse-y / x / forward-y pass for the FP32 passes (next kg_step)"""
+    _check(lib.kg_set_xy_fusion(1 if on else 0), "kg_set_xy_fusion")
+
+
+def kg_get_xy_fusion():
+    """(as set, used by the current context)"""
+    on, active = C.c_int(), C.c_int()
+    _check(lib.kg_get_xy_fusion(C.byref(on), C.byref(active)), "kg_get_xy_fusion")
+    return bool(on.value), bool(active.value)
 
 
 def kg_status():
