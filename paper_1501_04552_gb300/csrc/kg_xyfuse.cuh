@@ -55,6 +55,14 @@ struct XyShape {
     static_assert(NT <= 1024, "one CTA");
 };
 
+// every thread of every CTA of the cluster: the memory operations before it (stores into
+// other CTAs' shared memory included) are visible to every thread after it
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("fence.acq_rel.cluster;\n" ::: "memory");
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 // the column view of one column transform: rows of the slab (or of the idle area)
 template <class P>
 struct SlabCol {
@@ -139,6 +147,9 @@ __global__ void __launch_bounds__(XyShape<N, CL>::NT, 1)
             C v[8];
 #pragma unroll
             for (int s = 0; s < 8; s++) v[s] = col.get(j + TY * s);
+            // the column's rows are also its exchange space: every thread has read them
+            // before the first exchange writes over them
+            __syncthreads();
             fft<P, N>(v, j, tw, 1, col, sg);
             // the last stage leaves the outputs in registers; every exchange read is done
 #pragma unroll
@@ -154,7 +165,7 @@ __global__ void __launch_bounds__(XyShape<N, CL>::NT, 1)
             for (int lc = lane; lc < ncols; lc += 32) slab[row * LDC + lc] = W[zb + (size_t)row * NX + lc];
         __syncthreads();
         if (DO_YI) y_transforms(+1);
-        cluster.sync();   // every slab holds its columns in y
+        cluster_barrier();   // every slab holds its columns in y
         // x-lines of rows [rank RPC, (rank+1) RPC)
 #pragma unroll 1
         for (int xr = 0; xr < X::XROUNDS; xr++) {
@@ -165,7 +176,7 @@ __global__ void __launch_bounds__(XyShape<N, CL>::NT, 1)
             x_line_body<P, N, MODE_STEP, ClusterLine<S, N, CL>, ClusterLine<S, N, CL>>(line, line, j, lsm, tw, scale,
                                                                                       rlam, want_sum, st);
         }
-        cluster.sync();   // every remote write into this slab has landed
+        cluster_barrier();   // every remote write into this slab has landed
         y_transforms(-1);
         for (int row = warp; row < N; row += NWARPS)
             for (int lc = lane; lc < ncols; lc += 32) W[zb + (size_t)row * NX + lc] = slab[row * LDC + lc];

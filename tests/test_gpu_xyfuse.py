@@ -3,8 +3,11 @@ y of each z-plane in one kernel of thread-block clusters.
 
 The fused kernel runs the same transforms as the separate passes, so the field, the
 spectral state and the energies must agree with the separate-pass form to FP32
-rounding effects on F (the state is FP64; compiler contraction may differ between the
-kernels), and with the FP64 oracle to the FP32/FP64 split's 1e-5.  The step sequence of
+rounding effects (compiler contraction may differ between the kernels): on the FP64
+state they are damped by dt^2 |u|^2 (bound 1e-9); the energy's P = lam (h^3/4) sum u^4
+is summed from the FP32 values of u, so E carries FP32 rounding of P (P is below 1e-2
+of E here: bound 1e-9 of E).  Against the FP64 oracle the bound is the FP32/FP64
+split's 1e-5.  The step sequence of
 the fused form (first step of a call without the inverse y transforms, a closing inverse
 y pass) is checked by splitting the steps over several kg_step calls, by reading the
 energy between calls and by switching the fusion on and off mid-run.
@@ -67,7 +70,7 @@ def test_fused_matches_separate_passes(kg, N):
     u1, a1, b1, e1, s1 = run(kg, N, 0.02, chunks, True)
     assert rel(u1, u0) <= 1e-9
     assert rel(a1, a0) <= 1e-9 and rel(b1, b0) <= 1e-9
-    assert np.abs(e1 - e0).max() <= 1e-12 * np.abs(e0).max()
+    assert np.abs(e1 - e0).max() <= 1e-9 * np.abs(e0).max()
     assert s1["level"] == s0["level"] == sum(chunks)
     assert abs(s1["maxabs"] - s0["maxabs"]) <= 1e-6 * s0["maxabs"]   # max |u| of the last x pass
 
@@ -103,7 +106,7 @@ def test_fused_512_matches_separate_passes(kg):
     kg.kg_finalize()
     kg.kg_set_xy_fusion(False)
     assert rel(out[True][0], out[False][0]) <= 1e-9
-    assert np.abs(out[True][1] - out[False][1]).max() <= 1e-12 * abs(out[False][1][0])
+    assert np.abs(out[True][1] - out[False][1]).max() <= 1e-9 * abs(out[False][1][0])
 
 
 def test_toggle_mid_run(kg):
