@@ -399,6 +399,7 @@ def main():
             extras[other] = {"steps_per_s": round(steps / (o_ms * 1e-3), 2), "ms_per_step": round(o_ms / steps, 4),
                              "kernel_ms": {n: round(t, 4) for n, t in zip(o_names, o_k)},
                              "step_hbm_frac": round(o_step_bytes / (o_ms / steps * 1e-3) / 1e9 / peak, 4)}
+        extras["mixed_xy_fused"] = xy_fused_point(kg, stream, torch, u0, NG, local, peak)
         extras["cufft_torch"] = torch_fft_point(u0, local)
         if NG == 512:
             extras["paper_table1_protocol"] = {p: paper_protocol(kg, stream, torch, u0, NG, local, p)
@@ -470,6 +471,43 @@ def precision_split(kg, torch, u0, NG, local, steps):
     for prec in ("df64", "mixed"):
         out[prec]["rel_l2_vs_fp64"] = float(np.linalg.norm(fields[prec] - ref) / nrm)
     out["steps"] = steps
+    return out
+
+
+def xy_fused_point(kg, stream, torch, u0, NG, local, peak):
+    """the FP32 passes with the inverse y, x and forward y transforms of each z-plane fused
+    in thread-block clusters (kg_set_xy_fusion): steps/s, the fused kernel's device time
+    and its HBM fraction for its algorithmic 2 W (W = S/2), against the same steps with
+    the separate passes (x, y, y: 6 W)"""
+    out = {}
+    for fused in (False, True):
+        kg.kg_set_options(precision="mixed", energy_every=ENERGY_EVERY)
+        kg.kg_set_xy_fusion(fused)
+        d_u0 = torch.from_numpy(u0).to(f"cuda:{local}")
+        kg.kg_init_device(NG, L_BOX, DT, d_u0, None)
+        del d_u0
+        kg.kg_step(5)
+        kg.kg_energy(allow_drift=True)
+        stream.synchronize()
+        steps = 2 * ENERGY_EVERY
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kg.kg_step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        k = [t / steps for t in kg.kg_step_timed(steps)]
+        kg.kg_finalize()
+        w_bytes = NG * NG * (NG // 2 + 1) * 8
+        if fused:
+            out["fused"] = {"steps_per_s": round(1e3 / ms, 2), "ms_per_step": round(ms, 4),
+                            "xy_kernel_ms": round(k[0], 4), "z_ms": round(k[2], 4),
+                            "xy_hbm_frac": round(2 * w_bytes / (k[0] * 1e-3) / 1e9 / peak, 4)}
+        else:
+            out["separate"] = {"steps_per_s": round(1e3 / ms, 2), "ms_per_step": round(ms, 4),
+                               "x_yf_yi_ms": round(k[0] + k[1] + k[5], 4),
+                               "x_yf_yi_hbm_frac": round(6 * w_bytes / ((k[0] + k[1] + k[5]) * 1e-3) / 1e9 / peak, 4)}
+    kg.kg_set_xy_fusion(False)
     return out
 
 

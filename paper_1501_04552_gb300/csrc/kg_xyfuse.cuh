@@ -53,6 +53,8 @@ struct XyShape {
     static_assert(CW >= 1 && (N / 2) % CL == 0 && N % CL == 0, "slabs and x-line blocks tile the plane");
     static_assert(DUMMY <= XBUF, "idle column transforms exchange inside the x-line buffers");
     static_assert(NT <= 1024, "one CTA");
+    // resident CTAs per SM compiled for: two when both fit in an SM's shared memory
+    static constexpr int MINB = 2 * (SLAB + XBUF) * 8 + 2048 <= 232448 ? 2 : 1;
 };
 
 // every thread of every CTA of the cluster: the memory operations before it (stores into
@@ -111,7 +113,7 @@ struct ClusterLine {
 // DO_YI: start with the inverse y transforms (W holds the output of a z pass); without
 // it W already holds the y-inverse (the first step after set-up or a previous call).
 template <int N, int CL, bool DO_YI>
-__global__ void __launch_bounds__(XyShape<N, CL>::NT, 1)
+__global__ void __launch_bounds__(XyShape<N, CL>::NT, XyShape<N, CL>::MINB)
     k_xy_cluster(float2* __restrict__ W, KgDev* __restrict__ dev, double* __restrict__ part_sum,
                  double* __restrict__ part_max, const float2* __restrict__ tw, double scale, double lam) {
     typedef PrecF32 P;
