@@ -76,20 +76,24 @@ def algorithmic_bytes(prec, n=N_GRID):
     s_bytes = n * n * (n // 2 + 1) * 16
     w = s_bytes if prec in ("fp64", "df64") else s_bytes // 2
     per_kernel = {"x": 2 * w, "yf": 2 * w, "zf": 2 * w, "update": 2 * w + 3 * s_bytes, "zi": 2 * w, "yi": 2 * w,
-                  "z": 2 * w + 3 * s_bytes}
+                  "z": 2 * w + 3 * s_bytes, "xy": 2 * w}
     return per_kernel, 8 * w + 3 * s_bytes
 
 
 def kernel_groups(k_ms):
     """names and device ms of a step's kernel groups from kg_step_timed: x, yf, z (the
     fused z pass: forward z FFT, update, inverse z FFT), yi when the update and inverse-z
-    slots are empty; else the six separate groups"""
+    slots are empty; xy (the cluster-fused inverse y, x and forward y pass), z and yi
+    (the inverse y pass that closes a kg_step call, once per call) when the forward-y slot
+    is empty too; else the six separate groups"""
+    if k_ms[1] == 0.0 and k_ms[3] == 0.0 and k_ms[4] == 0.0:
+        return ["xy", "z", "yi"], [k_ms[0], k_ms[2], k_ms[5]]
     if k_ms[3] == 0.0 and k_ms[4] == 0.0:
         return ["x", "yf", "z", "yi"], [k_ms[0], k_ms[1], k_ms[2], k_ms[5]]
     return ["x", "yf", "zf", "update", "zi", "yi"], list(k_ms)
 
 
-KERNEL_NAMES = {"x": "k_pass_x", "z": "k_zstep", "update": "k_update"}
+KERNEL_NAMES = {"x": "k_pass_x", "z": "k_zstep", "update": "k_update", "xy": "k_xy_cluster"}
 
 
 # FP32 issue peak of the GPU: 152 SMs x 128 FP32 lanes x 2.07 GHz (max SM clock), one
@@ -114,6 +118,28 @@ def df64_fp32_ops(n):
     per_pair = n * (22 + fft_point + 4 + 42 + fft_point) + (n // 2 + 1) * 52
     col_points = n * n * (n // 2 + 1)
     return {"x": pairs * per_pair, "col": col_points * fft_point}
+
+
+def df64_fft_point_ops(n):
+    """FP32 operations per point of a length-n double-float transform of the FFT engine
+    (the counts of df64_fp32_ops): a radix-8 DFT 444 per 8 points, radix-4 128 per 4,
+    radix-2 32 per 2; every stage after the first applies a twiddle product (38) to
+    (R-1)/R of the points; the last stage renormalises (6 per point)"""
+    lg = n.bit_length() - 1
+    radices = [8] * (lg // 3) + ([1 << (lg % 3)] if lg % 3 else [])
+    dft = {8: 444 / 8.0, 4: 128 / 4.0, 2: 32 / 2.0}
+    ops = sum(dft[r] for r in radices) + 6
+    ops += sum((r - 1) / r * 38 for r in radices[1:])
+    return ops
+
+
+def df64_step_ops(n):
+    """FP32 operations of one double-float step of an n^3 grid: the paired x pass and four
+    column transforms (forward y, forward and inverse z, inverse y) of the half spectrum"""
+    f = df64_fft_point_ops(n)
+    pairs = n * n // 2
+    x = pairs * (n * (22 + f + 4 + 42 + f) + (n // 2 + 1) * 52)
+    return x + 4 * n * n * (n // 2 + 1) * f
 
 
 def peaks():
@@ -251,6 +277,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other precisions and the cuFFT point")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle sample (profiling runs)")
     ap.add_argument("--ens-steps", type=int, default=200, help="fixed steps of the ensemble comparison")
+    ap.add_argument("--no-ranker", action="store_true", help="skip the learned-ranker study (about two minutes)")
+    ap.add_argument("--xy-fusion", action="store_true",
+                    help="time the FP32 passes with the cluster-fused xy pass (with --precision mixed)")
     ap.add_argument("--grid", type=int, default=N_GRID, help="grid size (512 is the benchmark; smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -276,6 +305,7 @@ def main():
 
     NG = args.grid
     w = I.bump_noise(NG)
+    kg.kg_set_xy_fusion(args.xy_fusion)
     u0 = w["u0"]
     stream = torch.cuda.Stream()
     kg.kg_set_stream(stream)
@@ -413,6 +443,17 @@ def main():
     if not args.no_extras and rank == 0:
         ens = ensemble_point(kg, prec, args.ens_steps, torch, stream, early_exit=True)
         ens["mixed"] = ensemble_point(kg, "mixed", args.ens_steps, torch, stream)
+    ranker_study = None
+    if not args.no_extras and not args.no_ranker and rank == 0:
+        # the learned blow-up ranker on the GPU: 4096 solver-labelled 64^3 runs (T = 10),
+        # training of the 6-128-128-2 network, a 65 536-point Sobol sweep, the top 1024 and
+        # 1024 uniform points re-solved by the plain solver as judge, the boundary bracketed
+        # at 32 values of s with and without the network
+        from paper_1501_04552_gb300 import ranker
+        kg.kg_set_options()
+        t0 = time.perf_counter()
+        ranker_study = ranker.run()
+        ranker_study["wall_seconds"] = round(time.perf_counter() - t0, 1)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -441,7 +482,7 @@ def main():
                 "energy_series": {"every": ENERGY_EVERY, "first": energies[0] if energies else None,
                                   "max_rel_drift": (max(abs(e - energies[0]) for e in energies) / abs(energies[0])
                                                     if energies else None)},
-                "other_precisions": extras, "ensemble": ens}
+                "other_precisions": extras, "ensemble": ens, "ranker_study": ranker_study}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -621,6 +662,7 @@ def ensemble_point(kg, prec, steps, torch, stream, early_exit=False):
     kg.kg_ens_init(Ns, L_BOX, DT, A, s)
     bps, order = kg.kg_ens_tune(2)                 # tuned on a throw-away copy
     kg.kg_ens_init(Ns, L_BOX, DT, A, s)
+    sched = kg.kg_ens_schedule()[0]
     kg.kg_ens_run(3)
     done, ms = kg.kg_ens_run(steps, 0.0)
     res = kg.kg_ens_results()
@@ -659,7 +701,23 @@ def ensemble_point(kg, prec, steps, torch, stream, early_exit=False):
     # harmonic combination of the per-size rates
     plain_rate = tot_steps / (tot_ms * 1e-3)
     plain_by_size = {"%d^3" % n: round(v[1] / (v[0] * 1e-3), 1) for n, v in by_size.items() if v[1]}
+    # roofline of the ensemble step: the double-float transforms are bound by FP32 issue
+    # (operation count of df64_step_ops), the FP32 ones by HBM (11 S or 7 S per instance)
+    n64, n128 = int((Ns == 64).sum()), int((Ns == 128).sum())
+    if prec == "df64":
+        ops = n64 * df64_step_ops(64) + n128 * df64_step_ops(128)
+        bound_rate = FP32_ISSUE_PEAK / ops * len(Ns)
+        roof = {"bound": "alu", "unit": "instance-steps/s", "peak": round(bound_rate, 1),
+                "frac": round(ens_rate / bound_rate, 4), "peak_kind": "FP32 issue peak / double-float operations"}
+    else:
+        per = lambda n: n * n * (n // 2 + 1) * 16 * (11 if prec == "fp64" else 7)
+        byts = n64 * per(64) + n128 * per(128)
+        hbm, kind = peaks()
+        bound_rate = hbm * 1e9 / byts * len(Ns)
+        roof = {"bound": "hbm", "unit": "instance-steps/s", "peak": round(bound_rate, 1),
+                "frac": round(ens_rate / bound_rate, 4), "peak_kind": kind + " HBM / algorithmic bytes"}
     return {"instances": int(len(Ns)), "grids": "256 x 64^3 + 256 x 128^3", "steps": int(done),
+            "roofline": roof, "tuned_schedule": sched,
             "instance_steps_per_s": round(ens_rate, 1), "plain_loop_instance_steps_per_s": round(plain_rate, 1),
             "speedup_vs_plain": round(ens_rate / plain_rate, 3), "precision": prec,
             "plain_loop_by_grid": plain_by_size,

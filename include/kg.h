@@ -264,10 +264,28 @@ int kg_ens_features(double* shells);
 /* u^n of instance i (N^3 doubles, host memory). */
 int kg_ens_fetch(int i, double* u);
 
-/* Time every launch shape (CTAs per SM x unit order) for `steps` steps on the current
- * ensemble, keep the fastest, and remember it for later kg_ens_init calls with the
- * same precision and grid mix.  Advances the ensemble. */
+/* Time every launch shape for `steps` steps on the current ensemble, keep the fastest,
+ * and remember it for later kg_ens_init calls with the same precision and grid mix (and,
+ * with kg_ens_set_tune_cache, in the cache file).  A shape is a schedule -- bit 0: column
+ * tiles of half the default width; bit 1: the short radix stage first in transforms whose
+ * length is not a power of 8 (the 128^3 instances) -- times the unit order (0: instance
+ * order, 1: larger grids first) times the resident CTAs per SM.  Every shape computes the
+ * same step; schedules with bit 1 differ from the others in the rounding of the
+ * transforms only.  Advances the ensemble.  blocks_per_sm and order may be NULL. */
 int kg_ens_tune(int steps, int* blocks_per_sm, int* order);
+
+/* The launch shape of the current ensemble (any pointer may be NULL). */
+int kg_ens_schedule(int* sched, int* blocks_per_sm, int* order);
+
+/* Force a launch shape: sched 0..3, blocks_per_sm >= 1 (capped at what fits), order 0 or
+ * 1.  KG_EINVAL otherwise, KG_ESTATE without an ensemble. */
+int kg_ens_set_schedule(int sched, int blocks_per_sm, int order);
+
+/* Text file in which kg_ens_tune stores its choice, keyed by precision, grid mix, device
+ * name and SM count (one line per key, rewritten through a temporary file), and from which
+ * kg_ens_init takes the shape when this process has not tuned that key.  NULL or "": no
+ * file (default). */
+int kg_ens_set_tune_cache(const char* path);
 
 int kg_ens_finalize(void);
 

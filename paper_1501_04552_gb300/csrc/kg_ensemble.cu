@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -26,12 +27,89 @@ namespace {
 constexpr int kGraphSteps = 10;
 
 // launch shape chosen by kg_ens_tune, reused by later kg_ens_init calls with the
-// same precision and the same numbers of 64^3 and 128^3 instances
+// same precision and the same numbers of 64^3 and 128^3 instances (in this process, and
+// through the cache file of kg_ens_set_tune_cache in later ones)
 struct Tuned {
     bool valid = false;
-    int prec = 0, n64 = 0, n128 = 0, bps = 2, order = 1;
+    int prec = 0, n64 = 0, n128 = 0, sched = 0, bps = 2, order = 1;
 };
 Tuned g_tuned;
+std::string g_cache_path;   // kg_ens_set_tune_cache ("" = no file)
+
+int efail(int code, const std::string& msg);
+
+// the device the cache entries are keyed by: name (spaces as '_') and SM count
+std::string device_key() {
+    int dev = 0, sms = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    sms = prop.multiProcessorCount;
+    std::string name = prop.name;
+    for (char& ch : name)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    return name + " " + std::to_string(sms);
+}
+
+// cache file: one line per key, "kgens <prec> <n64> <n128> <device> <sms> <sched> <bps> <order> <ms>"
+bool cache_lookup(int prec, int n64, int n128, Tuned* out) {
+    if (g_cache_path.empty()) return false;
+    FILE* f = std::fopen(g_cache_path.c_str(), "r");
+    if (!f) return false;
+    const std::string dk = device_key();
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        char tag[16], dname[256];
+        int pr, a, b, sms, sc, bp, od;
+        double ms;
+        if (std::sscanf(line, "%15s %d %d %d %255s %d %d %d %d %lf", tag, &pr, &a, &b, dname, &sms, &sc, &bp, &od,
+                        &ms) != 10)
+            continue;
+        if (std::string(tag) != "kgens" || pr != prec || a != n64 || b != n128) continue;
+        if (std::string(dname) + " " + std::to_string(sms) != dk) continue;
+        if (sc < 0 || sc >= kEnsSchedules || bp < 1 || (od != 0 && od != 1)) continue;
+        out->valid = true;
+        out->prec = prec;
+        out->n64 = n64;
+        out->n128 = n128;
+        out->sched = sc;
+        out->bps = bp;
+        out->order = od;
+        found = true;
+    }
+    std::fclose(f);
+    return found;
+}
+
+// replace (or add) the entry of t in the cache file; the file is rewritten through a
+// temporary file and a rename, so a reader never sees half of it
+int cache_store(const Tuned& t, double ms) {
+    if (g_cache_path.empty()) return KG_OK;
+    std::vector<std::string> keep;
+    const std::string dk = device_key();
+    if (FILE* f = std::fopen(g_cache_path.c_str(), "r")) {
+        char line[512];
+        while (std::fgets(line, sizeof(line), f)) {
+            char tag[16], dname[256];
+            int pr, a, b, sms;
+            const bool parsed = std::sscanf(line, "%15s %d %d %d %255s %d", tag, &pr, &a, &b, dname, &sms) == 6;
+            const bool same = parsed && std::string(tag) == "kgens" && pr == t.prec && a == t.n64 && b == t.n128 &&
+                              std::string(dname) + " " + std::to_string(sms) == dk;
+            if (!same) keep.push_back(line);
+        }
+        std::fclose(f);
+    }
+    const std::string tmp = g_cache_path + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return efail(KG_EINVAL, "cannot write the tune cache " + tmp);
+    for (const auto& l : keep) std::fputs(l.c_str(), f);
+    std::fprintf(f, "kgens %d %d %d %s %d %d %d %.4f\n", t.prec, t.n64, t.n128, dk.c_str(), t.sched, t.bps, t.order,
+                 ms);
+    const bool ok = std::fclose(f) == 0;
+    if (!ok || std::rename(tmp.c_str(), g_cache_path.c_str()) != 0)
+        return efail(KG_EINVAL, "cannot replace the tune cache " + g_cache_path);
+    return KG_OK;
+}
 
 void count_sizes(const std::vector<int>& Ns, int* n64, int* n128) {
     *n64 = 0;
@@ -143,7 +221,7 @@ struct Ens {
     double* phys = nullptr;     // physical scratch of the largest grid
     cudaStream_t stream = nullptr;
     const PassLaunch* pl = nullptr;
-    int bps = 1, grid = 0, order = 0, nsm = 0;
+    int bps = 1, grid = 0, order = 0, nsm = 0, sched = 0;
     double threshold = -1.0;
     int missing = 0;
     long long spin_limit = 1ll << 24;
@@ -229,7 +307,7 @@ int rebuild_graph(Ens* e) {
     cudaGraph_t g = nullptr;
     KG_ECK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
-    for (int s = 0; s < kGraphSteps && le == cudaSuccess; s++) le = e->pl->ens_step(p, e->grid, e->stream);
+    for (int s = 0; s < kGraphSteps && le == cudaSuccess; s++) le = e->pl->ens_step(p, e->grid, e->sched, e->stream);
     cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
     if (le != cudaSuccess || ce != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -248,9 +326,10 @@ int check_status(Ens* e) {
     return KG_OK;
 }
 
-int set_shape(Ens* e, int bps, int order) {
-    const int maxb = e->pl->ens_blocks_per_sm();
+int set_shape(Ens* e, int sched, int bps, int order) {
+    const int maxb = e->pl->ens_blocks_per_sm(sched);
     if (maxb < 1) return efail(KG_ECUDA, "ensemble kernel cannot be resident (occupancy 0)");
+    e->sched = sched;
     e->bps = std::max(1, std::min(bps, maxb));
     e->grid = e->bps * e->nsm;
     e->order = order;
@@ -262,7 +341,7 @@ int set_shape(Ens* e, int bps, int order) {
 // one run of n steps without the graph (used for remainders and by the tuner)
 int launch_steps(Ens* e, int n) {
     const EnsParams p = make_params(e);
-    for (int s = 0; s < n; s++) KG_ECK(e->pl->ens_step(p, e->grid, e->stream));
+    for (int s = 0; s < n; s++) KG_ECK(e->pl->ens_step(p, e->grid, e->sched, e->stream));
     return KG_OK;
 }
 
@@ -381,8 +460,11 @@ int kg_ens_init(int count, const int* Ns, double L, double dt, const double* A, 
     {
         int n64, n128;
         count_sizes(e->Ns, &n64, &n128);
-        const bool use = g_tuned.valid && g_tuned.prec == e->prec && g_tuned.n64 == n64 && g_tuned.n128 == n128;
-        KG_ETRY(set_shape(e, use ? g_tuned.bps : 2, use ? g_tuned.order : 1));
+        Tuned t;
+        const bool use = (g_tuned.valid && g_tuned.prec == e->prec && g_tuned.n64 == n64 && g_tuned.n128 == n128 &&
+                          (t = g_tuned, true)) ||
+                         cache_lookup(e->prec, n64, n128, &t);
+        KG_ETRY(set_shape(e, use ? t.sched : 0, use ? t.bps : 2, use ? t.order : 1));
     }
 #undef KG_ETRY
     g_ens = e;
@@ -481,41 +563,71 @@ int kg_ens_tune(int steps, int* blocks_per_sm, int* order) {
     if (!e) return efail(KG_ESTATE, "kg_ens_tune before kg_ens_init");
     if (steps < 1) return efail(KG_EINVAL, "steps < 1");
     // the candidates advance the ensemble itself: tune on a throw-away ensemble and
-    // initialise the measured one afterwards (the choice is kept for it)
-    const int maxb = e->pl->ens_blocks_per_sm();
+    // initialise the measured one afterwards (the choice is kept for it).  Candidates:
+    // every schedule (tile width x stage order) x unit order x resident CTAs per SM
     float best = 1e30f;
-    int bb = 1, bo = 0;
-    for (int o = 0; o < 2; o++) {
-        for (int b = 1; b <= maxb; b++) {
-            int rc = set_shape(e, b, o);
-            if (rc) return rc;
-            rc = launch_steps(e, 1);   // warm-up
-            if (rc) return rc;
-            KG_ECK(cudaEventRecord(e->ev0, e->stream));
-            rc = launch_steps(e, steps);
-            if (rc) return rc;
-            KG_ECK(cudaEventRecord(e->ev1, e->stream));
-            KG_ECK(cudaEventSynchronize(e->ev1));
-            int rs = check_status(e);
-            if (rs) return rs;
-            float t = 0.f;
-            KG_ECK(cudaEventElapsedTime(&t, e->ev0, e->ev1));
-            if (t < best) {
-                best = t;
-                bb = b;
-                bo = o;
+    int bs = 0, bb = 1, bo = 0;
+    for (int sc = 0; sc < kEnsSchedules; sc++) {
+        const int maxb = e->pl->ens_blocks_per_sm(sc);
+        for (int o = 0; o < 2; o++) {
+            for (int b = 1; b <= maxb; b++) {
+                int rc = set_shape(e, sc, b, o);
+                if (rc) return rc;
+                rc = launch_steps(e, 1);   // warm-up
+                if (rc) return rc;
+                KG_ECK(cudaEventRecord(e->ev0, e->stream));
+                rc = launch_steps(e, steps);
+                if (rc) return rc;
+                KG_ECK(cudaEventRecord(e->ev1, e->stream));
+                KG_ECK(cudaEventSynchronize(e->ev1));
+                int rs = check_status(e);
+                if (rs) return rs;
+                float t = 0.f;
+                KG_ECK(cudaEventElapsedTime(&t, e->ev0, e->ev1));
+                if (t < best) {
+                    best = t;
+                    bs = sc;
+                    bb = b;
+                    bo = o;
+                }
             }
         }
     }
-    int rc = set_shape(e, bb, bo);
+    int rc = set_shape(e, bs, bb, bo);
     if (rc) return rc;
     g_tuned.valid = true;
     g_tuned.prec = e->prec;
     count_sizes(e->Ns, &g_tuned.n64, &g_tuned.n128);
+    g_tuned.sched = bs;
     g_tuned.bps = bb;
     g_tuned.order = bo;
+    rc = cache_store(g_tuned, best / steps);
+    if (rc) return rc;
     if (blocks_per_sm) *blocks_per_sm = bb;
     if (order) *order = bo;
+    return KG_OK;
+}
+
+int kg_ens_schedule(int* sched, int* blocks_per_sm, int* order) {
+    Ens* e = g_ens;
+    if (!e) return efail(KG_ESTATE, "kg_ens_schedule before kg_ens_init");
+    if (sched) *sched = e->sched;
+    if (blocks_per_sm) *blocks_per_sm = e->bps;
+    if (order) *order = e->order;
+    return KG_OK;
+}
+
+int kg_ens_set_schedule(int sched, int blocks_per_sm, int order) {
+    Ens* e = g_ens;
+    if (!e) return efail(KG_ESTATE, "kg_ens_set_schedule before kg_ens_init");
+    if (sched < 0 || sched >= kEnsSchedules || blocks_per_sm < 1 || (order != 0 && order != 1))
+        return efail(KG_EINVAL, "kg_ens_set_schedule: sched in [0, 4), blocks_per_sm >= 1, order 0 or 1");
+    KG_ECK(cudaStreamSynchronize(e->stream));
+    return set_shape(e, sched, blocks_per_sm, order);
+}
+
+int kg_ens_set_tune_cache(const char* path) {
+    g_cache_path = path ? path : "";
     return KG_OK;
 }
 

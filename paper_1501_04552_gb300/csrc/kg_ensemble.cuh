@@ -56,10 +56,24 @@ struct EnsParams {
     long long spin_limit;
 };
 
+// Launch schedules of the ensemble step, chosen by the autotuner (kg_ens_tune):
+//   bit 0: column tiles of half the default width (64-byte instead of 128-byte rows;
+//          twice the tiles per unit);
+//   bit 1: the short radix stage first in transforms whose length is not a power of 8
+//          (128-point columns and x-line pairs, 32-point FP32 x-lines; FftShape).
+// Every schedule computes the same step; a tile width changes nothing of the arithmetic,
+// the stage order changes the rounding of the transforms (double-float/FP32 level).
+constexpr int kEnsSchedules = 4;
+template <int SCHED>
+struct EnsSched {
+    static constexpr int cdiv = (SCHED & 1) ? 2 : 1;
+    static constexpr bool remfirst = (SCHED & 2) != 0;
+};
+
 // work units per pass for a grid of size N (256 threads each)
-template <class P, int N>
+template <class P, int N, int SCHED = 0>
 struct EnsUnits {
-    static constexpr int C = ColShape<P>::C;
+    static constexpr int C = ColShape<P>::C / EnsSched<SCHED>::cdiv;
     static constexpr int TPP = (N / 2 + 1 + C - 1) / C;              // column tiles per plane
     static constexpr int TPU = kEnsThreads / (C * N / 8);             // tiles per unit
     static constexpr int col_units = (N * TPP + TPU - 1) / TPU;
@@ -100,11 +114,12 @@ __device__ __forceinline__ bool ens_barrier(const EnsParams& p, unsigned nblocks
     return s_ok != 0;
 }
 
-template <class P, int N>
+template <class P, int N, int SCHED>
 __device__ __forceinline__ void ens_unit(const EnsParams& p, int ii, int unit, int pass, bool active_z,
                                          int inst_phase, unsigned* maxkey_row, typename P::S* sm) {
     typedef typename P::S S;
-    typedef EnsUnits<P, N> U;
+    typedef EnsUnits<P, N, SCHED> U;
+    constexpr bool RF = EnsSched<SCHED>::remfirst;
     constexpr int NH = N / 2 + 1;
     const EnsInst& in = p.inst[ii];
     const EnsTab& tb = (N == 64) ? p.tab64 : p.tab128;
@@ -120,15 +135,17 @@ __device__ __forceinline__ void ens_unit(const EnsParams& p, int ii, int unit, i
             const int pi = threadIdx.x / XP::T, jp = threadIdx.x % XP::T;
             const size_t pair = (size_t)unit * (U::LPU / 2) + pi;
             LineSmemX<P, false> lsm{sm + pi * XP::PADN, 0u, 0u};
-            x_pair_body<P, N, MODE_STEP>(W + 2 * pair * NH, jp, lsm, tw, 1.0 / ((double)N * N * N),
-                                         P::from_f64(p.lam), false, st);
+            x_pair_body<P, N, MODE_STEP, LineSmemX<P, false>, RF>(W + 2 * pair * NH, jp, lsm, tw,
+                                                                  1.0 / ((double)N * N * N), P::from_f64(p.lam),
+                                                                  false, st);
         } else {
             constexpr int T = N / 16;
             const int li = threadIdx.x / T, j = threadIdx.x % T;
             const size_t line = (size_t)unit * U::LPU + li;
             LineSmem<P> lsm{sm + li * XShape<N>::PADM};
-            x_line_body<P, N, MODE_STEP>(W + line * NH, W + line * NH, j, lsm, tw, 1.0 / ((double)N * N * N),
-                                         P::from_f64(p.lam), false, st);
+            x_line_body<P, N, MODE_STEP, const S*, S* __restrict__, RF>(W + line * NH, W + line * NH, j, lsm, tw,
+                                                                        1.0 / ((double)N * N * N),
+                                                                        P::from_f64(p.lam), false, st);
         }
         const unsigned k2 = st.fkey();
         const unsigned wmax = __reduce_max_sync(0xffffffffu, k2);
@@ -145,16 +162,17 @@ __device__ __forceinline__ void ens_unit(const EnsParams& p, int ii, int unit, i
         const bool valid = tile_ok && kx < NH;
         ColSmem<P, C> csm{sm + sub * (N * C), c};
         if (pass == 1) {
-            col_body<P, P, P, N, -1, C>(W, W, (size_t)plane * N * NH + kx, NH, valid, j, csm, tw);
+            col_body<P, P, P, N, -1, C, RF>(W, W, (size_t)plane * N * NH + kx, NH, valid, j, csm, tw);
         } else if (pass == 3) {
-            col_body<P, P, P, N, +1, C>(W, W, (size_t)plane * N * NH + kx, NH, valid, j, csm, tw);
+            col_body<P, P, P, N, +1, C, RF>(W, W, (size_t)plane * N * NH + kx, NH, valid, j, csm, tw);
         } else {
             double2* cur = inst_phase ? in.S1 : in.S0;
             double2* old = inst_phase ? in.S0 : in.S1;
             NSum q;
             q.s = 0.0;
             q.c = 0.0;
-            z_body<P, N>(W, cur, old, kx, plane, valid, j, csm, tw, tb.coef, tb.w2, p.inv_dt, active_z, false, q);
+            z_body<P, N, 0, C, RF>(W, cur, old, kx, plane, valid, j, csm, tw, tb.coef, tb.w2, p.inv_dt, active_z, false,
+                                   q);
         }
     }
 }
@@ -217,7 +235,7 @@ struct EnsMinBlocks<PrecF32> {
     static constexpr int value = 4;
 };
 
-template <class P>
+template <class P, int SCHED>
 __global__ void __launch_bounds__(kEnsThreads, EnsMinBlocks<P>::value) k_ens_step(EnsParams p) {
     typedef typename P::S S;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -245,8 +263,8 @@ __global__ void __launch_bounds__(kEnsThreads, EnsMinBlocks<P>::value) k_ens_ste
             if (pass >= 2 && live) live = !(((volatile unsigned*)keys)[i] > p.thr_key);
             int n = 0;
             if (live) {
-                if (s_n128[i]) n = (pass == 0) ? EnsUnits<P, 128>::x_units : EnsUnits<P, 128>::col_units;
-                else n = (pass == 0) ? EnsUnits<P, 64>::x_units : EnsUnits<P, 64>::col_units;
+                if (s_n128[i]) n = (pass == 0) ? EnsUnits<P, 128, SCHED>::x_units : EnsUnits<P, 128, SCHED>::col_units;
+                else n = (pass == 0) ? EnsUnits<P, 64, SCHED>::x_units : EnsUnits<P, 64, SCHED>::col_units;
             }
             s_pref[k + 1] = n;
         }
@@ -262,8 +280,8 @@ __global__ void __launch_bounds__(kEnsThreads, EnsMinBlocks<P>::value) k_ens_ste
             }
             const int ii = p.order_idx[lo];
             const int local = unit - s_pref[lo];
-            if (!s_n128[ii]) ens_unit<P, 64>(p, ii, local, pass, true, s_phase0[ii], keys, sm);
-            else ens_unit<P, 128>(p, ii, local, pass, true, s_phase0[ii], keys, sm);
+            if (!s_n128[ii]) ens_unit<P, 64, SCHED>(p, ii, local, pass, true, s_phase0[ii], keys, sm);
+            else ens_unit<P, 128, SCHED>(p, ii, local, pass, true, s_phase0[ii], keys, sm);
             __syncthreads();
         }
         if (pass == 3) break;

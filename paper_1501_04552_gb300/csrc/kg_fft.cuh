@@ -44,14 +44,20 @@ enum { MODE_STEP = 0, MODE_PEEK = 1 };
 
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
 
-template <int n>
+// Stage plan of a length-n transform: radix-8 stages and, when log2 n is not a multiple
+// of 3, one radix-2 or radix-4 stage -- last (REMFIRST = false, the default) or first.
+// Both orders compute the same DFT; the autotuner of the batched ensemble picks one.
+template <int n, bool REMFIRST = false>
 struct FftShape {
     static_assert(n >= 8 && (n & (n - 1)) == 0, "power-of-two length >= 8");
     static constexpr int lg = ilog2c(n);
     static constexpr int n8 = lg / 3;              // radix-8 stages
-    static constexpr int rem = 1 << (lg % 3);      // radix of the final stage (1: none)
+    static constexpr int rem = 1 << (lg % 3);      // radix of the short stage (1: none)
     static constexpr int stages = n8 + (rem > 1 ? 1 : 0);
     static constexpr int T = n / 8;                // threads per line
+    static constexpr bool kRemFirst = REMFIRST && rem > 1;
+    __host__ __device__ static constexpr int radix(int s) { return kRemFirst ? (s == 0 ? rem : 8) : (s < n8 ? 8 : rem); }
+    __host__ __device__ static constexpr int span(int s) { return s == 0 ? 1 : span(s - 1) * radix(s - 1); }   // Ns of stage s
 };
 
 // The transform sign sg (-1 forward, +1 inverse) is an ordinary argument: where a call
@@ -221,13 +227,13 @@ struct LineSmemX {
 // (k = b mod Ns), takes the R-point DFT and writes y[(b - k) R + k + r Ns].
 // twmul: table length / n.
 // ---------------------------------------------------------------------------
-template <class P, int n, int STAGE, class SM, bool TWPOW = false>
+template <class P, int n, int STAGE, class SM, bool TWPOW = false, bool REMFIRST = false>
 __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw,
                                           int twmul, SM& sm, int sg) {
     typedef cx<typename P::R> C;
-    typedef FftShape<n> Sh;
-    constexpr int RADIX = (STAGE < Sh::n8) ? 8 : Sh::rem;
-    constexpr int Ns = 1 << (3 * STAGE);
+    typedef FftShape<n, REMFIRST> Sh;
+    constexpr int RADIX = Sh::radix(STAGE);
+    constexpr int Ns = Sh::span(STAGE);
     constexpr int T = Sh::T;
     constexpr int Q = 8 / RADIX;
     constexpr bool LAST = (STAGE == Sh::stages - 1);
@@ -288,15 +294,16 @@ __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, cons
 }
 
 // full length-n transform, unnormalised, sign sg; in and out: v[s] = x[j + T s].
-// TWPOW: radix-8 stages form the twiddle powers by products instead of table loads
-template <class P, int n, class SM, bool TWPOW = false>
+// TWPOW: radix-8 stages form the twiddle powers by products instead of table loads;
+// REMFIRST: the short stage first (FftShape)
+template <class P, int n, class SM, bool TWPOW = false, bool REMFIRST = false>
 __device__ __forceinline__ void fft(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw, int twmul,
                                     SM& sm, int sg) {
-    typedef FftShape<n> Sh;
-    fft_stage<P, n, 0, SM, TWPOW>(v, j, tw, twmul, sm, sg);
-    if constexpr (Sh::stages > 1) fft_stage<P, n, 1, SM, TWPOW>(v, j, tw, twmul, sm, sg);
-    if constexpr (Sh::stages > 2) fft_stage<P, n, 2, SM, TWPOW>(v, j, tw, twmul, sm, sg);
-    if constexpr (Sh::stages > 3) fft_stage<P, n, 3, SM, TWPOW>(v, j, tw, twmul, sm, sg);
+    typedef FftShape<n, REMFIRST> Sh;
+    fft_stage<P, n, 0, SM, TWPOW, REMFIRST>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 1) fft_stage<P, n, 1, SM, TWPOW, REMFIRST>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 2) fft_stage<P, n, 2, SM, TWPOW, REMFIRST>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 3) fft_stage<P, n, 3, SM, TWPOW, REMFIRST>(v, j, tw, twmul, sm, sg);
 }
 
 // ---------------------------------------------------------------------------

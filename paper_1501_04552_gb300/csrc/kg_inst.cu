@@ -99,8 +99,10 @@ cudaError_t colc_to_f64(int N, const void* W, double2* out, size_t ps, size_t rs
     return Lp::colc_to_f64(N, W, out, ps, rs, nplanes, tw, st);
 }
 #elif KG_PART == 4
-cudaError_t ens_step(const EnsParams& p, int grid, cudaStream_t st) { return Lp::ens_step(p, grid, st); }
-int ens_blocks_per_sm() { return Lp::ens_blocks_per_sm(); }
+cudaError_t ens_step(const EnsParams& p, int grid, int sched, cudaStream_t st) {
+    return Lp::ens_step(p, grid, sched, st);
+}
+int ens_blocks_per_sm(int sched) { return Lp::ens_blocks_per_sm(sched); }
 #else
 #error "KG_PART out of range"
 #endif

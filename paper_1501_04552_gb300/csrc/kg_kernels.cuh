@@ -52,7 +52,8 @@ __device__ __forceinline__ void x_load_c2r(LIN line, int j, const typename P::S*
 // cube, R2C and write-back.  The line is read from Lin (global memory, or the line's
 // landing slot in shared memory, which may be lsm's own storage) and written to L
 // (pointers, or element accessors as for x_load_c2r; every read precedes every write).
-template <class P, int N, int MODE, class LIN = const typename P::S*, class LOUT = typename P::S* __restrict__>
+template <class P, int N, int MODE, class LIN = const typename P::S*, class LOUT = typename P::S* __restrict__,
+          bool RF = false>
 __device__ __forceinline__ void x_line_body(LIN Lin, LOUT L, int j,
                                             LineSmem<P>& lsm, const typename P::S* __restrict__ tw, double scale,
                                             typename P::R rlam, bool want_sum, Stats<P>& st) {
@@ -66,7 +67,7 @@ __device__ __forceinline__ void x_line_body(LIN Lin, LOUT L, int j,
 #pragma unroll 1
     for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
         // the FP32 x pass is bound by the L1TEX pipe: twiddle powers by products there
-        fft<P, M, LineSmem<P>, sizeof(typename P::R) == 4>(v, j, tw, 2, lsm, dir == 0 ? +1 : -1);
+        fft<P, M, LineSmem<P>, sizeof(typename P::R) == 4, RF>(v, j, tw, 2, lsm, dir == 0 ? +1 : -1);
         if (dir == 0) {
 #pragma unroll
             for (int s = 0; s < 8; s++) {
@@ -186,7 +187,7 @@ __device__ __forceinline__ void x_pair_unpack(typename P::S* __restrict__ L1, ty
     lsm.sync();
 }
 
-template <class P, int N, int MODE, class SM>
+template <class P, int N, int MODE, class SM, bool RF = false>
 __device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int j, SM& lsm,
                                             const typename P::S* __restrict__ tw, double scale, typename P::R rlam,
                                             bool want_sum, Stats<P>& st) {
@@ -198,7 +199,7 @@ __device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int 
     x_pair_load<P, N>(L1, L2, j, v);
 #pragma unroll 1
     for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
-        fft<P, N>(v, j, tw, 1, lsm, dir == 0 ? +1 : -1);
+        fft<P, N, SM, false, RF>(v, j, tw, 1, lsm, dir == 0 ? +1 : -1);
         if (dir == 0) {
 #pragma unroll
             for (int s = 0; s < 8; s++) {
@@ -371,7 +372,7 @@ struct ColStep {
 
 // one column (T = N/8 threads, thread j) of a tile; valid == false for the columns
 // of the last tile beyond kx = N/2 (they compute on zeros and store nothing)
-template <class Pin, class P, class Pout, int N, int SIGN, int CW>
+template <class Pin, class P, class Pout, int N, int SIGN, int CW, bool RF = false>
 __device__ __forceinline__ void col_body(const typename Pin::S* src, typename Pout::S* dst, size_t base,
                                          size_t row_stride, bool valid, int j, ColSmem<P, CW>& csm,
                                          const typename P::S* __restrict__ tw) {
@@ -383,7 +384,7 @@ __device__ __forceinline__ void col_body(const typename Pin::S* src, typename Po
         if (valid) v[s] = Convert<Pin, P>::go(Pin::load(src[base + (size_t)(j + T * s) * row_stride]));
         else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
     }
-    fft<P, N>(v, j, tw, 1, csm, SIGN);
+    fft<P, N, ColSmem<P, CW>, false, RF>(v, j, tw, 1, csm, SIGN);
     if (valid) {
 #pragma unroll
         for (int s = 0; s < 8; s++) dst[base + (size_t)(j + T * s) * row_stride] = Pout::pack(Convert<P, Pout>::go(v[s]));
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(CW * N / 8) k_col_sel(const double2* src0, con
 // asynchronous copies issued before the forward FFT: 0 none, 1 uh^n only (st_sm holds
 // 8 nt double2, slot s nt + tid), 2 both arrays (16 nt double2, uh^n at (2s) nt + tid,
 // uh^{n-1} at (2s+1) nt + tid); nt = threads of the CTA, tid = this thread's slot.
-template <class P, int N, int PF = 0, int CW = ColShape<P>::C>
+template <class P, int N, int PF = 0, int CW = ColShape<P>::C, bool RF = false>
 __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const double2* __restrict__ cur,
                                        double2* __restrict__ old, int kx, int ky, bool valid, int j,
                                        ColSmem<P, CW>& csm, const typename P::S* __restrict__ tw,
@@ -469,7 +470,7 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
     constexpr bool kShare = sizeof(typename P::S) == 16;
 #pragma unroll(kShare ? 1 : 2)
     for (int dir = 0; dir < 2; dir++) {
-        fft<P, N>(v, j, tw, 1, csm, dir == 0 ? -1 : +1);
+        fft<P, N, ColSmem<P, CW>, false, RF>(v, j, tw, 1, csm, dir == 0 ? -1 : +1);
         if (dir == 1) break;
         if (PF > 0) cp_async_wait_all();   // each thread reads back only its own copies
         const int my = ky <= N / 2 ? ky : ky - N;

@@ -40,9 +40,10 @@ struct PassLaunch {
     cudaError_t (*update)(int N, void* W, double2* S0, double2* S1, KgDev* dev, double* part_sum, const double2* coef,
                           const double* w2tab, double inv_dt, const C4Args* c4, cudaStream_t st);
     int (*update_parts)(int N);
-    // one persistent cooperative launch of an ensemble step (kg_ensemble.cuh)
-    cudaError_t (*ens_step)(const EnsParams& p, int grid, cudaStream_t st);
-    int (*ens_blocks_per_sm)();
+    // one persistent cooperative launch of an ensemble step (kg_ensemble.cuh) in launch
+    // schedule sched (0 .. kEnsSchedules-1), and the CTAs per SM that schedule can hold
+    cudaError_t (*ens_step)(const EnsParams& p, int grid, int sched, cudaStream_t st);
+    int (*ens_blocks_per_sm)(int sched);
     int (*x_parts)(int N);
     size_t store_bytes;  // bytes of one complex value of W
     // complex field (full N^3 spectrum, N columns per plane): x pass, column FFTs,

@@ -392,9 +392,12 @@ struct Launchers {
         }
     }
 
-    static size_t ens_smem() {
-        typedef EnsUnits<P, 64> U64;
-        typedef EnsUnits<P, 128> U128;
+    // the ensemble step (kg_ensemble.cuh); schedules differ in tile shape and stage order,
+    // not in shared memory (a unit's tiles always hold 2048 values)
+    template <int SCHED>
+    static size_t ens_smem_s() {
+        typedef EnsUnits<P, 64, SCHED> U64;
+        typedef EnsUnits<P, 128, SCHED> U128;
         size_t a = (size_t)U64::LPU * XShape<64>::PADM, b = (size_t)U128::LPU * XShape<128>::PADM;
         size_t c = (size_t)U64::TPU * 64 * U64::C, d = (size_t)U128::TPU * 128 * U128::C;
         size_t m = a > b ? a : b;
@@ -402,27 +405,48 @@ struct Launchers {
         m = m > d ? m : d;
         return m * sizeof(S);
     }
-    static int ens_blocks_per_sm() {
-        if (set_smem(k_ens_step<P>, ens_smem()) != cudaSuccess) return 0;
+    template <int SCHED>
+    static int ens_blocks_per_sm_s() {
+        if (set_smem(k_ens_step<P, SCHED>, ens_smem_s<SCHED>()) != cudaSuccess) return 0;
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<P>, kEnsThreads, ens_smem()) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ens_step<P, SCHED>, kEnsThreads, ens_smem_s<SCHED>()) !=
+            cudaSuccess)
             return 0;
         return n;
     }
-    static cudaError_t ens_step(const EnsParams& p, int grid, cudaStream_t st) {
-        cudaError_t e = set_smem(k_ens_step<P>, ens_smem());
+    static int ens_blocks_per_sm(int sched) {
+        switch (sched) {
+            case 0: return ens_blocks_per_sm_s<0>();
+            case 1: return ens_blocks_per_sm_s<1>();
+            case 2: return ens_blocks_per_sm_s<2>();
+            case 3: return ens_blocks_per_sm_s<3>();
+            default: return 0;
+        }
+    }
+    template <int SCHED>
+    static cudaError_t ens_step_s(const EnsParams& p, int grid, cudaStream_t st) {
+        cudaError_t e = set_smem(k_ens_step<P, SCHED>, ens_smem_s<SCHED>());
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(kEnsThreads);
-        cfg.dynamicSmemBytes = ens_smem();
+        cfg.dynamicSmemBytes = ens_smem_s<SCHED>();
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, k_ens_step<P>, p);
+        return cudaLaunchKernelEx(&cfg, k_ens_step<P, SCHED>, p);
+    }
+    static cudaError_t ens_step(const EnsParams& p, int grid, int sched, cudaStream_t st) {
+        switch (sched) {
+            case 0: return ens_step_s<0>(p, grid, st);
+            case 1: return ens_step_s<1>(p, grid, st);
+            case 2: return ens_step_s<2>(p, grid, st);
+            case 3: return ens_step_s<3>(p, grid, st);
+            default: return cudaErrorInvalidValue;
+        }
     }
 };
 

@@ -92,6 +92,9 @@ _sig = {
     "kg_ens_features": ([_vp], C.c_int),
     "kg_ens_fetch": ([C.c_int, _vp], C.c_int),
     "kg_ens_tune": ([C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "kg_ens_schedule": ([C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "kg_ens_set_schedule": ([C.c_int, C.c_int, C.c_int], C.c_int),
+    "kg_ens_set_tune_cache": ([C.c_char_p], C.c_int),
     "kg_ens_finalize": ([], C.c_int),
     "kg_gaussian_features": ([C.c_int, C.c_int, C.c_double, _vp, _vp, _vp], C.c_int),
     "kg_mlp_param_count": ([], C.c_int),
@@ -394,6 +397,21 @@ def kg_ens_tune(steps=3):
     b, o = C.c_int(), C.c_int()
     _check(lib.kg_ens_tune(int(steps), C.byref(b), C.byref(o)), "kg_ens_tune")
     return b.value, o.value
+
+
+def kg_ens_schedule():
+    """(schedule, CTAs per SM, unit order) of the current ensemble"""
+    sc, b, o = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.kg_ens_schedule(C.byref(sc), C.byref(b), C.byref(o)), "kg_ens_schedule")
+    return sc.value, b.value, o.value
+
+
+def kg_ens_set_schedule(sched, blocks_per_sm, order):
+    _check(lib.kg_ens_set_schedule(int(sched), int(blocks_per_sm), int(order)), "kg_ens_set_schedule")
+
+
+def kg_ens_set_tune_cache(path):
+    _check(lib.kg_ens_set_tune_cache(None if path is None else os.fsencode(path)), "kg_ens_set_tune_cache")
 
 
 def kg_ens_finalize():

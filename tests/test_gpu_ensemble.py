@@ -136,3 +136,68 @@ def test_barrier_timeout_is_reported_not_hung(kg, monkeypatch):
     done, _ = kg.kg_ens_run(5)
     assert done == 5
     kg.kg_ens_finalize()
+
+
+@pytest.mark.parametrize("prec", ["df64", "mixed"])
+def test_every_schedule_computes_the_same_step(kg, prec):
+    """the autotuner's schedules against schedule 0: half-width tiles change nothing of the
+    arithmetic (bitwise); the short radix stage first changes the rounding of the 128-point
+    transforms only (double-float: 1e-13; FP32 passes: 1e-9 of the FP64 state)"""
+    dt, steps = 0.005, 23
+    kg.kg_set_options(precision=prec)
+    fields = {}
+    for sched in range(4):
+        kg.kg_ens_init(CASE_NS, L, dt, CASE_A, CASE_S)
+        kg.kg_ens_set_schedule(sched, 2, 1)
+        assert kg.kg_ens_schedule() == (sched, 2, 1)
+        kg.kg_ens_run(steps)
+        fields[sched] = [kg.kg_ens_fetch(i) for i in range(len(CASE_NS))]
+        kg.kg_ens_finalize()
+    tol = 1e-13 if prec == "df64" else 1e-9
+    for i in range(len(CASE_NS)):
+        assert np.array_equal(fields[1][i], fields[0][i]), i
+        assert np.array_equal(fields[3][i], fields[2][i]), i
+        assert rel(fields[2][i], fields[0][i]) <= tol, (i, rel(fields[2][i], fields[0][i]))
+    kg.kg_set_options()
+
+
+def test_tuned_schedule_is_cached_and_not_slower(kg, tmp_path):
+    """kg_ens_tune searches schedule x unit order x CTAs per SM; its choice is written to the
+    cache file, read back by a later kg_ens_init, and is at least as fast as the default shape
+    (schedule 0, two CTAs per SM, larger grids first) on the same ensemble"""
+    Ns, A, s = I.ensemble_params(96, 11)
+    cache = str(tmp_path / "ens_tune.txt")
+    kg.kg_set_options(precision="df64")
+    kg.kg_ens_set_tune_cache(cache)
+    kg.kg_ens_init(Ns, L, 0.005, A, s)
+    kg.kg_ens_tune(2)
+    tuned = kg.kg_ens_schedule()
+    kg.kg_ens_finalize()
+    lines = [l.split() for l in open(cache)]
+    assert len(lines) == 1 and lines[0][0] == "kgens" and [int(x) for x in lines[0][6:9]] == list(tuned)
+
+    def timed(shape):
+        kg.kg_ens_init(Ns, L, 0.005, A, s)
+        if shape is not None:
+            kg.kg_ens_set_schedule(*shape)
+        got = kg.kg_ens_schedule()
+        kg.kg_ens_run(3)
+        best = min(kg.kg_ens_run(20)[1] for _ in range(3))
+        kg.kg_ens_finalize()
+        return got, best
+
+    got, t_tuned = timed(None)          # a fresh init takes the tuned shape
+    assert got == tuned
+    _, t_default = timed((0, 2, 1))
+    assert t_tuned <= 1.03 * t_default, (tuned, t_tuned, t_default)
+    # an entry for another grid mix (written as a later process would find it) is read
+    # back by kg_ens_init for that mix
+    dev = lines[0][4:6]
+    with open(cache, "a") as f:
+        f.write("kgens 1 5 3 %s %s 3 1 0 9.0\n" % (dev[0], dev[1]))
+    mixNs = np.array([64] * 5 + [128] * 3, dtype=np.int32)
+    kg.kg_ens_init(mixNs, L, 0.005, A[:8], s[:8])
+    assert kg.kg_ens_schedule() == (3, 1, 0)
+    kg.kg_ens_finalize()
+    kg.kg_ens_set_tune_cache(None)
+    kg.kg_set_options()
