@@ -106,14 +106,14 @@ FP64_PEAK = 598e9
 def df64_fp32_ops(n):
     """FP32 operations of the double-float FFT kernels at grid n, counted from the
     definitions of the double-float arithmetic (Knuth two-sum 6 + low parts 2 = 8 per
-    unnormalised add, 19 per FMA-split dot product = one component of a twiddle product,
-    3 per renormalisation, 7 per double-float product; sign flips and integer work not
-    counted).  Radix-8 DFT without renormalisation: 24 complex adds (384) + the two
-    sqrt(1/2) rotations (60) = 444; the last stage renormalises its 8 outputs (+48); a
-    stage after the first applies 7 twiddle products (+266).  Returns per-launch counts
+    unnormalised add, 16 per unnormalised FMA-split dot product = one component of a
+    twiddle product, 4 per unnormalised product by a constant, 3 per renormalisation;
+    sign flips and integer work not counted).  Radix-8 DFT: 24 complex adds (384) + the two
+    sqrt(1/2) rotations (48) = 432; the last stage renormalises its 8 outputs (+48); a
+    stage after the first applies 7 twiddle products (+224).  Returns per-launch counts
     for the paired x pass and for one column pass (n = 512: three radix-8 stages)."""
     assert n == 512
-    fft_point = (444 + (444 + 266) + (444 + 266 + 48)) / 8.0      # 239 per point
+    fft_point = (432 + (432 + 224) + (432 + 224 + 48)) / 8.0      # 224 per point
     pairs = n * n // 2
     per_pair = n * (22 + fft_point + 4 + 42 + fft_point) + (n // 2 + 1) * 52
     col_points = n * n * (n // 2 + 1)
@@ -122,14 +122,14 @@ def df64_fp32_ops(n):
 
 def df64_fft_point_ops(n):
     """FP32 operations per point of a length-n double-float transform of the FFT engine
-    (the counts of df64_fp32_ops): a radix-8 DFT 444 per 8 points, radix-4 128 per 4,
-    radix-2 32 per 2; every stage after the first applies a twiddle product (38) to
+    (the counts of df64_fp32_ops): a radix-8 DFT 432 per 8 points, radix-4 128 per 4,
+    radix-2 32 per 2; every stage after the first applies a twiddle product (32) to
     (R-1)/R of the points; the last stage renormalises (6 per point)"""
     lg = n.bit_length() - 1
     radices = [8] * (lg // 3) + ([1 << (lg % 3)] if lg % 3 else [])
-    dft = {8: 444 / 8.0, 4: 128 / 4.0, 2: 32 / 2.0}
+    dft = {8: 432 / 8.0, 4: 128 / 4.0, 2: 32 / 2.0}
     ops = sum(dft[r] for r in radices) + 6
-    ops += sum((r - 1) / r * 38 for r in radices[1:])
+    ops += sum((r - 1) / r * 32 for r in radices[1:])
     return ops
 
 
@@ -386,7 +386,7 @@ def main():
                 "kernels": per_kernel}
     if prec == "df64":
         roofline["limiter"] = ("arithmetic, not HBM: the double-float transforms are bound by FP32 issue (x and y "
-                               "passes 0.62-0.66 of it, ncu issue active 76-81 %), and the fused z pass adds the "
+                               "passes about 0.6-0.65 of it, ncu issue active 76-81 %), and the fused z pass adds the "
                                "FP64 update on the FP64 pipe (frac_pipes of roofline_alu.kernels.z); their HBM "
                                "fraction is low by construction")
     roofline_alu = None

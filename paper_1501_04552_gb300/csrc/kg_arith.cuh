@@ -69,11 +69,13 @@ __device__ __forceinline__ df df_add_lazy(df x, df y) {
 __device__ __forceinline__ df df_sub_lazy(df x, df y) { return df_add_lazy(x, df_make(-y.hi, -y.lo)); }
 __device__ __forceinline__ df df_norm(df x) { return fast_two_sum(x.hi, x.lo); }
 
-// a.hi b.hi + c.hi d.hi + (low-order terms) with one renormalisation: the two products
-// are split exactly by FMA, their high parts added by two-sum, and every remaining
-// term (product errors, cross terms with the low parts, the two-sum error) summed in
-// float before the final fast two-sum
-__device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
+// a.hi b.hi + c.hi d.hi + (low-order terms) without the final renormalisation: the two
+// products are split exactly by FMA, their high parts added by two-sum, and every
+// remaining term (product errors, cross terms with the low parts, the two-sum error)
+// summed in float into the low part.  The pair represents the dot product to within
+// u^2 (|ab| + |cd|) like df_add_lazy's results; inside a transform it only meets lazy
+// sums and further products, and a transform's last stage renormalises.
+__device__ __forceinline__ df df_dot2_lazy(df a, df b, df c, df d) {
     const float p1 = __fmul_rn(a.hi, b.hi);
     const float p2 = __fmul_rn(c.hi, d.hi);
     const df s = two_sum(p1, p2);
@@ -83,7 +85,16 @@ __device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
     e = __fmaf_rn(a.lo, b.hi, e);
     e = __fmaf_rn(c.hi, d.lo, e);
     e = __fmaf_rn(c.lo, d.hi, e);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, e));
+    return df_make(s.hi, __fadd_rn(s.lo, e));
+}
+
+// x y with the product's error taken by FMA and no final renormalisation (as df_dot2_lazy)
+__device__ __forceinline__ df df_mul_lazy(df x, df y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return df_make(p, e);
 }
 
 // multiplication by a power of two (exact unless it under/overflows)
@@ -195,6 +206,7 @@ struct PrecF64 {
     static __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
     static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return a; }
     static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) { return cmul(a, w); }
+    static __device__ __forceinline__ R rmul(R a, R c) { return a * c; }
     // x with its sign bit xor-ed with m (m = 0 or 0x80000000): exact negation on demand
     static __device__ __forceinline__ R flip(R x, unsigned m) {
         return __hiloint2double(__double2hiint(x) ^ (int)m, __double2loint(x));
@@ -217,6 +229,7 @@ struct PrecF32 {
     static __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
     static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return a; }
     static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) { return cmul(a, w); }
+    static __device__ __forceinline__ R rmul(R a, R c) { return a * c; }
     static __device__ __forceinline__ R flip(R x, unsigned m) { return __uint_as_float(__float_as_uint(x) ^ m); }
 };
 
@@ -242,10 +255,14 @@ struct PrecDF {
     static __device__ __forceinline__ R radd(R a, R b) { return df_add_lazy(a, b); }
     static __device__ __forceinline__ R rsub(R a, R b) { return df_sub_lazy(a, b); }
     static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return cmake<R>(df_norm(a.re), df_norm(a.im)); }
-    // (a.re w.re - a.im w.im, a.re w.im + a.im w.re), one renormalisation per component
+    // (a.re w.re - a.im w.im, a.re w.im + a.im w.re), left unnormalised (df_dot2_lazy):
+    // inside a transform a twiddle product is followed by lazy sums or another product,
+    // and the transform's last stage renormalises its outputs
     static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) {
-        return cmake<R>(df_dot2(a.re, w.re, -a.im, w.im), df_dot2(a.re, w.im, a.im, w.re));
+        return cmake<R>(df_dot2_lazy(a.re, w.re, -a.im, w.im), df_dot2_lazy(a.re, w.im, a.im, w.re));
     }
+    // a real constant times a (the sqrt(1/2) rotations of a radix-8 DFT), unnormalised
+    static __device__ __forceinline__ R rmul(R a, R c) { return df_mul_lazy(a, c); }
     static __device__ __forceinline__ R flip(R x, unsigned m) {
         return df_make(__uint_as_float(__float_as_uint(x.hi) ^ m), __uint_as_float(__float_as_uint(x.lo) ^ m));
     }

@@ -137,12 +137,12 @@ __device__ __forceinline__ void dft8(cx<typename P::R>* u, int sg) {
     const unsigned ms = sign_mask(sg), mns = sign_mask(-sg);
     {   // b1 *= exp(sg i pi/4) = (1 + sg i)/sqrt2:  (x.re - sg x.im, x.im + sg x.re) / sqrt2
         C x = b[1];
-        b[1] = cmake<R>(P::radd(x.re, P::flip(x.im, mns)) * r, P::radd(x.im, P::flip(x.re, ms)) * r);
+        b[1] = cmake<R>(P::rmul(P::radd(x.re, P::flip(x.im, mns)), r), P::rmul(P::radd(x.im, P::flip(x.re, ms)), r));
     }
     b[2] = mul_sgi<P>(b[2], sg);
     {   // b3 *= exp(sg 3 i pi/4) = (-1 + sg i)/sqrt2:  (-sg x.im - x.re, sg x.re - x.im) / sqrt2
         C x = b[3];
-        b[3] = cmake<R>(P::rsub(P::flip(x.im, mns), x.re) * r, P::rsub(P::flip(x.re, ms), x.im) * r);
+        b[3] = cmake<R>(P::rmul(P::rsub(P::flip(x.im, mns), x.re), r), P::rmul(P::rsub(P::flip(x.re, ms), x.im), r));
     }
     dft4<P>(a, sg);
     dft4<P>(b, sg);

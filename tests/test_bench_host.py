@@ -37,9 +37,11 @@ def test_algorithmic_bytes(bench):
 def test_double_float_operation_count(bench):
     ops = bench.df64_fp32_ops(512)
     points = 512 * 512 * 257
-    assert ops["col"] == points * 239                      # 239 FP32 operations per point and transform
+    assert ops["col"] == points * 224                      # 224 FP32 operations per point and transform
     pairs = 512 * 512 // 2
-    assert ops["x"] == pairs * (512 * (22 + 239 + 4 + 42 + 239) + 257 * 52)
+    assert ops["x"] == pairs * (512 * (22 + 224 + 4 + 42 + 224) + 257 * 52)
+    assert bench.df64_fft_point_ops(512) == 224
+    assert bench.df64_step_ops(512) == ops["x"] + 4 * ops["col"]
 
 
 def test_traffic_guard(bench, monkeypatch):
