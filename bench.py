@@ -107,15 +107,16 @@ def df64_fp32_ops(n):
     """FP32 operations of the double-float FFT kernels at grid n, counted from the
     definitions of the double-float arithmetic (Knuth two-sum 6 + low parts 2 = 8 per
     unnormalised add, 16 per unnormalised FMA-split dot product = one component of a
-    twiddle product, 4 per unnormalised product by a constant, 3 per renormalisation;
-    sign flips and integer work not counted).  Radix-8 DFT: 24 complex adds (384) + the two
-    sqrt(1/2) rotations (48) = 432; the last stage renormalises its 8 outputs (+48); a
-    stage after the first applies 7 twiddle products (+224).  Returns per-launch counts
-    for the paired x pass and for one column pass (n = 512: three radix-8 stages)."""
+    twiddle product, 4 per unnormalised product; sign flips and integer work not counted;
+    no transform renormalises its outputs).  Radix-8 DFT: 24 complex adds (384) + the two
+    sqrt(1/2) rotations (48) = 432; a stage after the first applies 7 twiddle products
+    (+224).  The paired x pass per pair and point: packing 16, two transforms, scale 4,
+    the max|u| key 2, the cube 24; unpacking 40 per output.  Returns per-launch counts for
+    the paired x pass and for one column pass (n = 512: three radix-8 stages)."""
     assert n == 512
-    fft_point = (432 + (432 + 224) + (432 + 224 + 48)) / 8.0      # 224 per point
+    fft_point = (432 + (432 + 224) + (432 + 224)) / 8.0      # 218 per point
     pairs = n * n // 2
-    per_pair = n * (22 + fft_point + 4 + 42 + fft_point) + (n // 2 + 1) * 52
+    per_pair = n * (16 + fft_point + 4 + 2 + 24 + fft_point) + (n // 2 + 1) * 40
     col_points = n * n * (n // 2 + 1)
     return {"x": pairs * per_pair, "col": col_points * fft_point}
 
@@ -124,11 +125,11 @@ def df64_fft_point_ops(n):
     """FP32 operations per point of a length-n double-float transform of the FFT engine
     (the counts of df64_fp32_ops): a radix-8 DFT 432 per 8 points, radix-4 128 per 4,
     radix-2 32 per 2; every stage after the first applies a twiddle product (32) to
-    (R-1)/R of the points; the last stage renormalises (6 per point)"""
+    (R-1)/R of the points"""
     lg = n.bit_length() - 1
     radices = [8] * (lg // 3) + ([1 << (lg % 3)] if lg % 3 else [])
     dft = {8: 432 / 8.0, 4: 128 / 4.0, 2: 32 / 2.0}
-    ops = sum(dft[r] for r in radices) + 6
+    ops = sum(dft[r] for r in radices)
     ops += sum((r - 1) / r * 32 for r in radices[1:])
     return ops
 
@@ -138,7 +139,7 @@ def df64_step_ops(n):
     column transforms (forward y, forward and inverse z, inverse y) of the half spectrum"""
     f = df64_fft_point_ops(n)
     pairs = n * n // 2
-    x = pairs * (n * (22 + f + 4 + 42 + f) + (n // 2 + 1) * 52)
+    x = pairs * (n * (16 + f + 4 + 2 + 24 + f) + (n // 2 + 1) * 40)
     return x + 4 * n * n * (n // 2 + 1) * f
 
 

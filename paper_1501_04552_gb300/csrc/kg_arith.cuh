@@ -207,6 +207,7 @@ struct PrecF64 {
     static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return a; }
     static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) { return cmul(a, w); }
     static __device__ __forceinline__ R rmul(R a, R c) { return a * c; }
+    static __device__ __forceinline__ R cube(R x, R lam) { return lam * (x * x * x); }
     // x with its sign bit xor-ed with m (m = 0 or 0x80000000): exact negation on demand
     static __device__ __forceinline__ R flip(R x, unsigned m) {
         return __hiloint2double(__double2hiint(x) ^ (int)m, __double2loint(x));
@@ -230,6 +231,7 @@ struct PrecF32 {
     static __device__ __forceinline__ cx<R> cnorm(cx<R> a) { return a; }
     static __device__ __forceinline__ cx<R> ctw(cx<R> a, cx<R> w) { return cmul(a, w); }
     static __device__ __forceinline__ R rmul(R a, R c) { return a * c; }
+    static __device__ __forceinline__ R cube(R x, R lam) { return lam * (x * x * x); }
     static __device__ __forceinline__ R flip(R x, unsigned m) { return __uint_as_float(__float_as_uint(x) ^ m); }
 };
 
@@ -263,6 +265,10 @@ struct PrecDF {
     }
     // a real constant times a (the sqrt(1/2) rotations of a radix-8 DFT), unnormalised
     static __device__ __forceinline__ R rmul(R a, R c) { return df_mul_lazy(a, c); }
+    // lam x^3 of the x pass, unnormalised: it feeds the forward transform's lazy sums
+    static __device__ __forceinline__ R cube(R x, R lam) {
+        return df_mul_lazy(lam, df_mul_lazy(df_mul_lazy(x, x), x));
+    }
     static __device__ __forceinline__ R flip(R x, unsigned m) {
         return df_make(__uint_as_float(__float_as_uint(x.hi) ^ m), __uint_as_float(__float_as_uint(x.lo) ^ m));
     }

@@ -227,7 +227,7 @@ struct LineSmemX {
 // (k = b mod Ns), takes the R-point DFT and writes y[(b - k) R + k + r Ns].
 // twmul: table length / n.
 // ---------------------------------------------------------------------------
-template <class P, int n, int STAGE, class SM, bool TWPOW = false, bool REMFIRST = false>
+template <class P, int n, int STAGE, class SM, bool TWPOW = false, bool REMFIRST = false, bool NORMLAST = true>
 __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw,
                                           int twmul, SM& sm, int sg) {
     typedef cx<typename P::R> C;
@@ -272,7 +272,7 @@ __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, cons
                     u[r] = P::ctw(u[r], twiddle<P>(tw, k * r * (n / (Ns * RADIX)) * twmul, sg));
             }
         }
-        dft<P, RADIX, LAST>(u, sg);
+        dft<P, RADIX, LAST && NORMLAST>(u, sg);
         if (LAST) {
 #pragma unroll
             for (int r = 0; r < RADIX; r++) out[q + r * Q] = u[r];
@@ -295,15 +295,17 @@ __device__ __forceinline__ void fft_stage(cx<typename P::R> (&v)[8], int j, cons
 
 // full length-n transform, unnormalised, sign sg; in and out: v[s] = x[j + T s].
 // TWPOW: radix-8 stages form the twiddle powers by products instead of table loads;
-// REMFIRST: the short stage first (FftShape)
-template <class P, int n, class SM, bool TWPOW = false, bool REMFIRST = false>
+// REMFIRST: the short stage first (FftShape); NORMLAST = false leaves the double-float
+// outputs unnormalised too, for consumers that take lazy sums of them or convert both
+// words exactly (everything but the statistics of u, which read the high word)
+template <class P, int n, class SM, bool TWPOW = false, bool REMFIRST = false, bool NORMLAST = true>
 __device__ __forceinline__ void fft(cx<typename P::R> (&v)[8], int j, const typename P::S* __restrict__ tw, int twmul,
                                     SM& sm, int sg) {
     typedef FftShape<n, REMFIRST> Sh;
-    fft_stage<P, n, 0, SM, TWPOW, REMFIRST>(v, j, tw, twmul, sm, sg);
-    if constexpr (Sh::stages > 1) fft_stage<P, n, 1, SM, TWPOW, REMFIRST>(v, j, tw, twmul, sm, sg);
-    if constexpr (Sh::stages > 2) fft_stage<P, n, 2, SM, TWPOW, REMFIRST>(v, j, tw, twmul, sm, sg);
-    if constexpr (Sh::stages > 3) fft_stage<P, n, 3, SM, TWPOW, REMFIRST>(v, j, tw, twmul, sm, sg);
+    fft_stage<P, n, 0, SM, TWPOW, REMFIRST, NORMLAST>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 1) fft_stage<P, n, 1, SM, TWPOW, REMFIRST, NORMLAST>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 2) fft_stage<P, n, 2, SM, TWPOW, REMFIRST, NORMLAST>(v, j, tw, twmul, sm, sg);
+    if constexpr (Sh::stages > 3) fft_stage<P, n, 3, SM, TWPOW, REMFIRST, NORMLAST>(v, j, tw, twmul, sm, sg);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,8 +383,9 @@ struct Stats<PrecDF> {
     df acc;
     unsigned int mx;
     __device__ __forceinline__ void init() { acc = df_make(0.f, 0.f); mx = 0u; }
+    // u may be unnormalised: the key is the float nearest hi + lo
     __device__ __forceinline__ void take(df u, bool want_sum) {
-        unsigned int key = __float_as_uint(u.hi) & 0x7FFFFFFFu;
+        unsigned int key = __float_as_uint(__fadd_rn(u.hi, u.lo)) & 0x7FFFFFFFu;
         mx = key > mx ? key : mx;
         if (want_sum) {
             df u2 = u * u;

@@ -153,7 +153,8 @@ __device__ __forceinline__ void x_pair_load(const typename P::S* __restrict__ L1
             X1 = conj(X1);
             X2 = conj(X2);
         }
-        v[s] = P::cnorm(cmake<R>(P::rsub(X1.re, X2.im), P::radd(X1.im, X2.re)));   // X1 + i X2
+        // X1 + i X2, left unnormalised: the transform's first stage takes lazy sums of it
+        v[s] = cmake<R>(P::rsub(X1.re, X2.im), P::radd(X1.im, X2.re));
     }
 }
 
@@ -175,7 +176,9 @@ __device__ __forceinline__ void x_pair_unpack(typename P::S* __restrict__ L1, ty
             const C Z = v[s];
             const C Zm = conj(lsm.get((N - k) & (N - 1)));
             const C A = P::cadd(Z, Zm), B = P::csub(Z, Zm);      // 2 X1, 2 i X2
-            C x1 = P::cnorm(A), x2 = P::cnorm(cmake<R>(B.im, -B.re));
+            // stored unnormalised: every reader of W starts with lazy sums or an exact
+            // conversion of both words
+            C x1 = A, x2 = cmake<R>(B.im, -B.re);
             x1.re = P::scale2(x1.re, 0.5);
             x1.im = P::scale2(x1.im, 0.5);
             x2.re = P::scale2(x2.re, 0.5);
@@ -199,7 +202,9 @@ __device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int 
     x_pair_load<P, N>(L1, L2, j, v);
 #pragma unroll 1
     for (int dir = 0; dir < (MODE == MODE_STEP ? 2 : 1); dir++) {
-        fft<P, N, SM, false, RF>(v, j, tw, 1, lsm, dir == 0 ? +1 : -1);
+        // outputs left unnormalised: the statistics read the rounded sum of both words, the
+        // cube and the unpacking take lazy products and sums
+        fft<P, N, SM, false, RF, false>(v, j, tw, 1, lsm, dir == 0 ? +1 : -1);
         if (dir == 0) {
 #pragma unroll
             for (int s = 0; s < 8; s++) {
@@ -211,8 +216,8 @@ __device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int 
             if (MODE == MODE_STEP) {
 #pragma unroll
                 for (int s = 0; s < 8; s++) {
-                    v[s].re = rlam * (v[s].re * v[s].re * v[s].re);
-                    v[s].im = rlam * (v[s].im * v[s].im * v[s].im);
+                    v[s].re = P::cube(v[s].re, rlam);
+                    v[s].im = P::cube(v[s].im, rlam);
                 }
             }
         }
@@ -384,7 +389,7 @@ __device__ __forceinline__ void col_body(const typename Pin::S* src, typename Po
         if (valid) v[s] = Convert<Pin, P>::go(Pin::load(src[base + (size_t)(j + T * s) * row_stride]));
         else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
     }
-    fft<P, N, ColSmem<P, CW>, false, RF>(v, j, tw, 1, csm, SIGN);
+    fft<P, N, ColSmem<P, CW>, false, RF, false>(v, j, tw, 1, csm, SIGN);   // outputs go to W or FP64
     if (valid) {
 #pragma unroll
         for (int s = 0; s < 8; s++) dst[base + (size_t)(j + T * s) * row_stride] = Pout::pack(Convert<P, Pout>::go(v[s]));
@@ -470,7 +475,7 @@ __device__ __forceinline__ void z_body(typename P::S* __restrict__ W, const doub
     constexpr bool kShare = sizeof(typename P::S) == 16;
 #pragma unroll(kShare ? 1 : 2)
     for (int dir = 0; dir < 2; dir++) {
-        fft<P, N, ColSmem<P, CW>, false, RF>(v, j, tw, 1, csm, dir == 0 ? -1 : +1);
+        fft<P, N, ColSmem<P, CW>, false, RF, false>(v, j, tw, 1, csm, dir == 0 ? -1 : +1);
         if (dir == 1) break;
         if (PF > 0) cp_async_wait_all();   // each thread reads back only its own copies
         const int my = ky <= N / 2 ? ky : ky - N;
@@ -726,7 +731,8 @@ __global__ void __launch_bounds__(ZStepShape<N>::NT, ZStepMinBlocks<P, N>::value
     constexpr bool kShare = sizeof(S) == 16;
 #pragma unroll(kShare ? 1 : 2)
     for (int dir = 0; dir < 2; dir++) {
-        fft<P, N>(v, j, tw, 1, csm, dir == 0 ? -1 : +1);
+        // F^n goes to the update through exact conversions of both words, uh^{n+1} to W
+        fft<P, N, ColSmem<P, C>, false, false, false>(v, j, tw, 1, csm, dir == 0 ? -1 : +1);
         if (dir == 1) break;
         // the run state is read only now, so that nothing of it is live across the
         // forward transform (at 64 registers: 132 -> 8 bytes of spills, 1.98 -> 1.91 ms

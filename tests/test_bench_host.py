@@ -37,10 +37,10 @@ def test_algorithmic_bytes(bench):
 def test_double_float_operation_count(bench):
     ops = bench.df64_fp32_ops(512)
     points = 512 * 512 * 257
-    assert ops["col"] == points * 224                      # 224 FP32 operations per point and transform
+    assert ops["col"] == points * 218                      # 218 FP32 operations per point and transform
     pairs = 512 * 512 // 2
-    assert ops["x"] == pairs * (512 * (22 + 224 + 4 + 42 + 224) + 257 * 52)
-    assert bench.df64_fft_point_ops(512) == 224
+    assert ops["x"] == pairs * (512 * (16 + 218 + 4 + 2 + 24 + 218) + 257 * 40)
+    assert bench.df64_fft_point_ops(512) == 218
     assert bench.df64_step_ops(512) == ops["x"] + 4 * ops["col"]
 
 
