@@ -96,8 +96,9 @@ def kernel_groups(k_ms):
 KERNEL_NAMES = {"x": "k_pass_x", "z": "k_zstep", "update": "k_update", "xy": "k_xy_cluster"}
 
 
-# FP32 issue peak of the GPU: 152 SMs x 128 FP32 lanes x 2.07 GHz (max SM clock), one
-# instruction per lane per clock
+# FP32 peak of the GPU's FMA pipes: 152 SMs x 128 FP32 lanes x 2.07 GHz (max SM clock), one
+# operation per lane per clock, whether issued as scalar FP32 instructions or as packed
+# FP32x2 ones (which take the pipe for two lane operations; profiles/fp_pipes_gb300.md)
 FP32_ISSUE_PEAK = 152 * 128 * 2.07e9
 # FP64 FMA rate measured on GB300 (2 per SM per clock; profiles/fp_pipes_gb300.md)
 FP64_PEAK = 598e9
@@ -386,10 +387,11 @@ def main():
                 "step_achieved": round(step_achieved, 1), "step_frac": round(step_achieved / peak, 4),
                 "kernels": per_kernel}
     if prec == "df64":
-        roofline["limiter"] = ("arithmetic, not HBM: the double-float transforms are bound by FP32 issue (x and y "
-                               "passes about 0.6-0.65 of it, ncu issue active 76-81 %), and the fused z pass adds the "
-                               "FP64 update on the FP64 pipe (frac_pipes of roofline_alu.kernels.z); their HBM "
-                               "fraction is low by construction")
+        roofline["limiter"] = ("arithmetic, not HBM: the double-float transforms are bound by the FP32 lanes of the "
+                               "FMA pipes (packed FP32x2 instructions; x and y passes about 0.62-0.70 of their peak, "
+                               "ncu FMA pipe 75 % busy with math-pipe-throttle stalls in the x pass), and the fused z "
+                               "pass adds the FP64 update on the FP64 pipe (frac_pipes of roofline_alu.kernels.z); "
+                               "their HBM fraction is low by construction")
     roofline_alu = None
     if prec == "df64" and NG == 512:
         ops = df64_fp32_ops(NG)
@@ -717,14 +719,14 @@ def ensemble_point(kg, prec, steps, torch, stream, early_exit=False):
     # harmonic combination of the per-size rates
     plain_rate = tot_steps / (tot_ms * 1e-3)
     plain_by_size = {"%d^3" % n: round(v[1] / (v[0] * 1e-3), 1) for n, v in by_size.items() if v[1]}
-    # roofline of the ensemble step: the double-float transforms are bound by FP32 issue
-    # (operation count of df64_step_ops), the FP32 ones by HBM (11 S or 7 S per instance)
+    # roofline of the ensemble step: the double-float transforms are bound by the FP32 lanes of
+    # the FMA pipes (operation count of df64_step_ops), the FP32 ones by HBM (11 S or 7 S per instance)
     n64, n128 = int((Ns == 64).sum()), int((Ns == 128).sum())
     if prec == "df64":
         ops = n64 * df64_step_ops(64) + n128 * df64_step_ops(128)
         bound_rate = FP32_ISSUE_PEAK / ops * len(Ns)
         roof = {"bound": "alu", "unit": "instance-steps/s", "peak": round(bound_rate, 1),
-                "frac": round(ens_rate / bound_rate, 4), "peak_kind": "FP32 issue peak / double-float operations"}
+                "frac": round(ens_rate / bound_rate, 4), "peak_kind": "FP32 lane peak / double-float operations"}
     else:
         per = lambda n: n * n * (n // 2 + 1) * 16 * (11 if prec == "fp64" else 7)
         byts = n64 * per(64) + n128 * per(128)

@@ -81,7 +81,8 @@ int make_tables(int N, int prec, double L, double dt, const AllocFn& alloc, Tabl
         std::vector<float4> v(N);
         for (int j = 0; j < N; j++) {
             const float rh = (float)t64[j].x, ih = (float)t64[j].y;
-            v[j] = make_float4(rh, (float)(t64[j].x - (double)rh), ih, (float)(t64[j].y - (double)ih));
+            // (re.hi, im.hi, re.lo, im.lo), the layout of a double-float value (PrecDF::S)
+            v[j] = make_float4(rh, ih, (float)(t64[j].x - (double)rh), (float)(t64[j].y - (double)ih));
         }
         rc = alloc(&t->tw, sizeof(float4) * N, "twiddles df");
         if (rc) return rc;

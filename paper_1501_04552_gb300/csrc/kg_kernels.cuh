@@ -43,8 +43,10 @@ __device__ __forceinline__ void x_load_c2r(LIN line, int j, const typename P::S*
         }
         C A = P::cadd(X, conj(Xp));
         C B = P::csub(X, conj(Xp));
-        const C w = kPow ? wr[s] : twiddle<P>(tw, k, +1);   // exp(+2 pi i k / N)
-        v[s] = P::cnorm(P::cadd(A, mul_i(P::ctw(B, w))));
+        C Bw;                                                // B exp(+2 pi i k / N)
+        if constexpr (kPow) Bw = P::ctw(B, wr[s]);
+        else Bw = P::ctw(B, twiddle<P>(tw, k, +1));
+        v[s] = P::cnorm(P::cadd(A, mul_i(Bw)));
     }
 }
 
@@ -101,8 +103,9 @@ __device__ __forceinline__ void x_line_body(LIN Lin, LOUT L, int j,
             C Zp = lsm.get((M - k) & (M - 1));
             C A = P::cadd(Z, conj(Zp));
             C B = P::csub(Z, conj(Zp));
-            const C w = kPow ? wf[s] : twiddle<P>(tw, k, -1);   // exp(-2 pi i k / N)
-            C D = mul_i(P::ctw(B, w));
+            C D;                                                // i B exp(-2 pi i k / N)
+            if constexpr (kPow) D = mul_i(P::ctw(B, wf[s]));
+            else D = mul_i(P::ctw(B, twiddle<P>(tw, k, -1)));
             C out = P::cnorm(P::csub(A, D));
             out.re = P::scale2(out.re, half);
             out.im = P::scale2(out.im, half);
@@ -154,7 +157,7 @@ __device__ __forceinline__ void x_pair_load(const typename P::S* __restrict__ L1
             X2 = conj(X2);
         }
         // X1 + i X2, left unnormalised: the transform's first stage takes lazy sums of it
-        v[s] = cmake<R>(P::rsub(X1.re, X2.im), P::radd(X1.im, X2.re));
+        v[s] = P::cadd_i(X1, X2);
     }
 }
 
@@ -178,13 +181,8 @@ __device__ __forceinline__ void x_pair_unpack(typename P::S* __restrict__ L1, ty
             const C A = P::cadd(Z, Zm), B = P::csub(Z, Zm);      // 2 X1, 2 i X2
             // stored unnormalised: every reader of W starts with lazy sums or an exact
             // conversion of both words
-            C x1 = A, x2 = cmake<R>(B.im, -B.re);
-            x1.re = P::scale2(x1.re, 0.5);
-            x1.im = P::scale2(x1.im, 0.5);
-            x2.re = P::scale2(x2.re, 0.5);
-            x2.im = P::scale2(x2.im, 0.5);
-            L1[k] = P::pack(x1);
-            L2[k] = P::pack(x2);
+            L1[k] = P::pack(P::cscale2(A, 0.5));
+            L2[k] = P::pack(P::cscale2(P::cmul_negi(B), 0.5));
         }
     }
     lsm.sync();
@@ -389,7 +387,7 @@ __device__ __forceinline__ void col_body(const typename Pin::S* src, typename Po
         if (valid) v[s] = Convert<Pin, P>::go(Pin::load(src[base + (size_t)(j + T * s) * row_stride]));
         else v[s] = cmake<R>(P::from_f64(0.0), P::from_f64(0.0));
     }
-    fft<P, N, ColSmem<P, CW>, false, RF, false>(v, j, tw, 1, csm, SIGN);   // outputs go to W or FP64
+    fft<P, N, ColSmem<P, CW>, false, RF, false, false>(v, j, tw, 1, csm, SIGN);   // outputs go to W or FP64
     if (valid) {
 #pragma unroll
         for (int s = 0; s < 8; s++) dst[base + (size_t)(j + T * s) * row_stride] = Pout::pack(Convert<P, Pout>::go(v[s]));
