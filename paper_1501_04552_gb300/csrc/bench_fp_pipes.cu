@@ -66,8 +66,9 @@ enum { K_FFMA, K_FFMA2, K_FFMA_XOR, K_FFMA2_XOR, K_DFMA, K_DADD, K_CVT, K_DF_SCA
 static const char* kNames[K_COUNT] = {"FFMA (16 chains)", "FFMA2 (8 chains)", "FFMA + XOR", "FFMA2 + XOR",
                                       "DFMA", "DADD", "cvt f32->f64->f32", "df butterflies, scalar",
                                       "df butterflies, packed"};
-// lane operations per chain step counted for the rate (the XOR and the conversions' pairs
-// count as described in the table of the summary)
+// lane operations per chain step counted for the rate: the XORs are not counted, each of the
+// two conversions of a round trip counts one, a butterfly step counts the scalar double-float
+// operations (8 lazy sums of 16 and 7 twiddle products of 32)
 static const double kOpsPerIter[K_COUNT] = {16, 16, 16, 16, 16, 16, 32, 8 * 16 + 7 * 32, 8 * 16 + 7 * 32};
 
 template <int K>
