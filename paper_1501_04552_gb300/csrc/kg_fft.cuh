@@ -376,6 +376,10 @@ struct Stats<PrecF64> {
         mx = key > mx ? key : mx;
         if (want_sum) sum.add(m2 * m2);
     }
+    __device__ __forceinline__ void take2(cx<double> u, bool want_sum) {
+        take(u.re, want_sum);
+        take(u.im, want_sum);
+    }
     __device__ __forceinline__ double total() const { return sum.value(); }
     __device__ __forceinline__ double maxval() const { return __longlong_as_double((long long)mx); }
     // float bits of max|u| (nan above inf above every finite value)
@@ -389,8 +393,13 @@ struct Stats<PrecF64> {
 template <>
 struct Stats<PrecDF> {
     df acc;
+    dfc acc2;   // the sums of take2, one per lane, unnormalised (non-negative terms)
     unsigned int mx;
-    __device__ __forceinline__ void init() { acc = df_make(0.f, 0.f); mx = 0u; }
+    __device__ __forceinline__ void init() {
+        acc = df_make(0.f, 0.f);
+        acc2.h = acc2.l = make_float2(0.f, 0.f);
+        mx = 0u;
+    }
     // u may be unnormalised: the key is the float nearest hi + lo
     __device__ __forceinline__ void take(df u, bool want_sum) {
         unsigned int key = __float_as_uint(__fadd_rn(u.hi, u.lo)) & 0x7FFFFFFFu;
@@ -400,13 +409,28 @@ struct Stats<PrecDF> {
             acc = acc + u2 * u2;
         }
     }
+    // both components of u at once (the two lines of a pair), on packed FP32x2 pairs
+    __device__ __forceinline__ void take2(cx<df> u, bool want_sum) {
+        const dfc x = PrecDF::split(u);
+        const float2 r = f2add(x.h, x.l);
+        const unsigned k0 = __float_as_uint(r.x) & 0x7FFFFFFFu, k1 = __float_as_uint(r.y) & 0x7FFFFFFFu;
+        mx = k0 > mx ? k0 : mx;
+        mx = k1 > mx ? k1 : mx;
+        if (want_sum) {
+            const dfc u2 = dfc_mul_lazy(x, x);
+            acc2 = dfc_add_lazy(acc2, dfc_mul_lazy(u2, u2));
+        }
+    }
     // complex field: m2 = |u|^2 >= 0; the key is |u|^2 and the sum takes |u|^4
     __device__ __forceinline__ void take_sq(df m2, bool want_sum) {
         const unsigned int key = __float_as_uint(m2.hi);
         mx = key > mx ? key : mx;
         if (want_sum) acc = acc + m2 * m2;
     }
-    __device__ __forceinline__ double total() const { return f2d_int(acc.hi) + f2d_int(acc.lo); }
+    __device__ __forceinline__ double total() const {
+        return (f2d_int(acc.hi) + f2d_int(acc.lo)) + ((f2d_int(acc2.h.x) + f2d_int(acc2.l.x)) +
+                                                      (f2d_int(acc2.h.y) + f2d_int(acc2.l.y)));
+    }
     __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
     __device__ __forceinline__ unsigned fkey() const { return mx; }
     __device__ __forceinline__ unsigned long long dkey() const {
@@ -426,6 +450,10 @@ struct Stats<PrecF32> {
             float u2 = u * u;
             acc = acc + df_make(u2 * u2, 0.f);
         }
+    }
+    __device__ __forceinline__ void take2(cx<float> u, bool want_sum) {
+        take(u.re, want_sum);
+        take(u.im, want_sum);
     }
     __device__ __forceinline__ void take_sq(float m2, bool want_sum) {
         const unsigned int key = __float_as_uint(m2);

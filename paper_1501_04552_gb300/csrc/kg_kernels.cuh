@@ -208,8 +208,7 @@ __device__ __forceinline__ void x_pair_body(typename P::S* __restrict__ L1, int 
             for (int s = 0; s < 8; s++) {
                 v[s].re = P::scale2(v[s].re, scale);   // u1, u2 at x = j + T s; scale = 1/N^3
                 v[s].im = P::scale2(v[s].im, scale);
-                st.take(v[s].re, want_sum);
-                st.take(v[s].im, want_sum);
+                st.take2(v[s], want_sum);
             }
             if (MODE == MODE_STEP) {
 #pragma unroll
@@ -590,15 +589,19 @@ template <class P>
 struct QTerm {
     typedef df T;
     static __device__ __forceinline__ T zero() { return df_make(0.f, 0.f); }
+    // the cancelling differences in FP64, then squares and sums in double-float left
+    // unnormalised: D, S and r S are sums of non-negative terms (n + a adds two values of
+    // the same mode), so an unnormalised pair still holds each to within u^2 of its size,
+    // and value() converts both words exactly
     static __device__ __forceinline__ T term(double n_re, double n_im, double2 a, double w2, double qr, bool twice) {
         const df dre = d2df_int(n_re - a.x), dim = d2df_int(n_im - a.y);
-        const df sre = d2df_int(n_re) + d2df_int(a.x), sim = d2df_int(n_im) + d2df_int(a.y);
-        const df D = dre * dre + dim * dim;
-        const df S = sre * sre + sim * sim;
-        df t = D + (d2df_int(w2) * d2df_int(qr)) * S;
+        const df sre = df_add_lazy(d2df_int(n_re), d2df_int(a.x)), sim = df_add_lazy(d2df_int(n_im), d2df_int(a.y));
+        const df D = df_add_lazy(df_mul_lazy(dre, dre), df_mul_lazy(dim, dim));
+        const df S = df_add_lazy(df_mul_lazy(sre, sre), df_mul_lazy(sim, sim));
+        const df t = df_add_lazy(D, df_mul_lazy(df_mul_lazy(d2df_int(w2), d2df_int(qr)), S));
         return twice ? df_scale2(t, 2.0f) : t;
     }
-    static __device__ __forceinline__ T add(T x, T y) { return x + y; }
+    static __device__ __forceinline__ T add(T x, T y) { return df_add_lazy(x, y); }
     static __device__ __forceinline__ T shfl_down(T x, int o) {
         return df_make(__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o));
     }
