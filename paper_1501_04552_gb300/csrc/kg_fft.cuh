@@ -431,6 +431,10 @@ struct Stats<PrecDF> {
         return (f2d_int(acc.hi) + f2d_int(acc.lo)) + ((f2d_int(acc2.h.x) + f2d_int(acc2.l.x)) +
                                                       (f2d_int(acc2.h.y) + f2d_int(acc2.l.y)));
     }
+    // the same sum as a double-float (unnormalised; every term is non-negative)
+    __device__ __forceinline__ df total_df() const {
+        return df_add_lazy(acc, df_add_lazy(df_make(acc2.h.x, acc2.l.x), df_make(acc2.h.y, acc2.l.y)));
+    }
     __device__ __forceinline__ double maxval() const { return f2d_int(__uint_as_float(mx)); }
     __device__ __forceinline__ unsigned fkey() const { return mx; }
     __device__ __forceinline__ unsigned long long dkey() const {
@@ -527,6 +531,27 @@ __device__ __forceinline__ unsigned long long block_max_key(unsigned long long k
 }
 
 // NT threads, a power of two; lane 0 of warp 0 ends with the block result
+// sum of one non-negative double-float value per thread of an NT-thread CTA on the FP32
+// pipe (unnormalised sums; the FP64 Neumaier reduction of block_reduce spends most of a
+// recording x pass's extra time in its dependent FP64 chain); the total lands in thread 0
+template <int NT>
+__device__ __forceinline__ df block_sum_df(df v, df* sm) {
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = df_add_lazy(v, df_make(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = l < NT / 32 ? sm[l] : df_make(0.f, 0.f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            v = df_add_lazy(v, df_make(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)));
+    }
+    return v;
+}
+
 template <int NT>
 __device__ __forceinline__ void block_reduce(NSum& v, double& mx, double* sh) {
     // sh: 3 * 32 doubles

@@ -1,5 +1,6 @@
 // kg_kernels.cuh -- kernel templates of the step passes, the set-up and the read-out.
 #pragma once
+#include <type_traits>
 #include "kg_fft.cuh"
 #include "kg_launch.h"
 
@@ -343,12 +344,18 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<P>::value) k_pass_x(type
     const unsigned long long key = block_max_key<kXThreads>(st.dkey(), kred);
     if (threadIdx.x == 0) part_max[blockIdx.x] = __longlong_as_double((long long)key);
     if (want_sum) {
-        NSum acc;
-        acc.s = st.total();
-        acc.c = 0.0;
-        double unused = 0.0;
-        block_reduce<kXThreads>(acc, unused, red);
-        if (threadIdx.x == 0) part_sum[blockIdx.x] = acc.value();
+        if constexpr (XPaired<P>::value && !std::is_same<P, PrecF64>::value) {
+            __shared__ df dred[kXThreads / 32];
+            const df t = block_sum_df<kXThreads>(st.total_df(), dred);
+            if (threadIdx.x == 0) part_sum[blockIdx.x] = f2d_int(t.hi) + f2d_int(t.lo);
+        } else {
+            NSum acc;
+            acc.s = st.total();
+            acc.c = 0.0;
+            double unused = 0.0;
+            block_reduce<kXThreads>(acc, unused, red);
+            if (threadIdx.x == 0) part_sum[blockIdx.x] = acc.value();
+        }
     }
 }
 
