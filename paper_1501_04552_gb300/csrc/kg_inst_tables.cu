@@ -20,7 +20,7 @@ const PassLaunch kLaunchDF = {
     &inst_df::zstep, &inst_df::zstep_parts,
     &inst_df::x_setup, &inst_df::x_readout, &inst_df::col_to_f64,
     &inst_df::xc_setup, &inst_df::xc_readout, &inst_df::colc_to_f64,
-    nullptr, nullptr};   // no fused xy pass: the double-float passes are bound by FP32 issue, not HBM
+    nullptr, nullptr};   // no fused xy pass: the double-float passes are bound by the FMA pipes, not HBM
 const PassLaunch kLaunchF32 = {
     KG_TABLE_COMMON(inst_f32, 8),
     &inst_f32::zstep, &inst_f32::zstep_parts,
