@@ -67,6 +67,9 @@ typedef struct kg_options {
     double nonlinearity;    /* lam, coefficient of u^3 (default 1.0 = Eq. (1); 0 = linear) */
     double blowup_threshold;/* > 0: freeze the state once max|u^n| exceeds it (default 0: off) */
     double drift_tol;       /* > 0: kg_energy returns KG_EDRIFT past this relative drift */
+    const char* tune_cache; /* batched ensemble: the autotuner's cache file, as kg_ens_set_tune_cache
+                             * (copied by kg_set_options; NULL leaves the current file, "" sets none;
+                             * kg_get_options returns the library's copy or NULL) */
 } kg_options;
 
 /* Set up the solver: N^3 grid of side L, time step dt, initial field u0 and
@@ -284,7 +287,7 @@ int kg_ens_set_schedule(int sched, int blocks_per_sm, int order);
 /* Text file in which kg_ens_tune stores its choice, keyed by precision, grid mix, device
  * name and SM count (one line per key, rewritten through a temporary file), and from which
  * kg_ens_init takes the shape when this process has not tuned that key.  NULL or "": no
- * file (default). */
+ * file (default).  The same setting as kg_options.tune_cache. */
 int kg_ens_set_tune_cache(const char* path);
 
 int kg_ens_finalize(void);

@@ -84,7 +84,7 @@ struct Ctx {
 };
 
 Ctx* g_ctx = nullptr;
-kg_options g_opt = {KG_DF64, 0, 1.0, 0.0, 0.0};
+kg_options g_opt = {KG_DF64, 0, 1.0, 0.0, 0.0, nullptr};
 int g_scheme = KG_SCHEME_EQ2;
 int g_xy_fusion = 0;   // kg_set_xy_fusion
 cudaStream_t g_user_stream = nullptr;
@@ -588,6 +588,7 @@ int p_from_state(Ctx* c, bool older, double* out) {
 namespace kg {
 // lets other translation units of the library report through kg_last_error()
 int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+const char* ens_tune_cache();   // kg_ensemble.cu
 }  // namespace kg
 
 // ===========================================================================
@@ -870,7 +871,9 @@ int kg_set_options(const kg_options* o) {
     if (o->energy_every < 0) return fail(KG_EINVAL, "energy_every < 0");
     if (!std::isfinite(o->nonlinearity) || !std::isfinite(o->blowup_threshold) || !std::isfinite(o->drift_tol))
         return fail(KG_EINVAL, "non-finite option");
+    if (o->tune_cache) kg_ens_set_tune_cache(o->tune_cache);   // copied; NULL leaves it as set
     g_opt = *o;
+    g_opt.tune_cache = nullptr;   // kg_get_options reports the library's own copy
     if (g_ctx) {
         // energy cadence and blow-up threshold apply at once; lam and precision at the next init
         Ctx* c = g_ctx;
@@ -889,6 +892,7 @@ int kg_set_options(const kg_options* o) {
 int kg_get_options(kg_options* o) {
     if (!o) return fail(KG_EINVAL, "options pointer is NULL");
     *o = g_opt;
+    o->tune_cache = kg::ens_tune_cache();
     return KG_OK;
 }
 

@@ -665,3 +665,8 @@ int kg_ens_finalize(void) {
 }
 
 }  // extern "C"
+
+namespace kg {
+// the autotuner's cache file for kg_get_options (NULL when there is none)
+const char* ens_tune_cache() { return g_cache_path.empty() ? nullptr : g_cache_path.c_str(); }
+}  // namespace kg

@@ -38,7 +38,7 @@ PRECISIONS = {"fp64": KG_FP64, "df64": KG_DF64, "mixed": KG_MIXED}
 
 class kg_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("energy_every", C.c_int), ("nonlinearity", C.c_double),
-                ("blowup_threshold", C.c_double), ("drift_tol", C.c_double)]
+                ("blowup_threshold", C.c_double), ("drift_tol", C.c_double), ("tune_cache", C.c_char_p)]
 
 
 class kg_mlp_cfg(C.Structure):
@@ -227,17 +227,22 @@ def kg_set_stream(stream):
     _check(lib.kg_set_stream(ptr), "kg_set_stream")
 
 
-def kg_set_options(precision=KG_DF64, energy_every=0, nonlinearity=1.0, blowup_threshold=0.0, drift_tol=0.0):
+def kg_set_options(precision=KG_DF64, energy_every=0, nonlinearity=1.0, blowup_threshold=0.0, drift_tol=0.0,
+                   tune_cache=None):
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
-    o = kg_options(int(precision), int(energy_every), float(nonlinearity), float(blowup_threshold), float(drift_tol))
+    path = None if tune_cache is None else os.fsencode(tune_cache)
+    o = kg_options(int(precision), int(energy_every), float(nonlinearity), float(blowup_threshold), float(drift_tol),
+                   path)
     _check(lib.kg_set_options(C.byref(o)), "kg_set_options")
 
 
 def kg_get_options():
     o = kg_options()
     _check(lib.kg_get_options(C.byref(o)), "kg_get_options")
-    return {f: getattr(o, f) for f, _ in kg_options._fields_}
+    d = {f: getattr(o, f) for f, _ in kg_options._fields_}
+    d["tune_cache"] = None if d["tune_cache"] is None else os.fsdecode(d["tune_cache"])
+    return d
 
 
 def kg_set_scheme(scheme=KG_SCHEME_EQ2):

@@ -54,7 +54,7 @@ def test_options_round_trip_and_validation(kg):
     kg.kg_set_options(precision="mixed", energy_every=10, nonlinearity=0.5, blowup_threshold=1e3, drift_tol=1e-3)
     o = kg.kg_get_options()
     assert o == {"precision": kg.KG_MIXED, "energy_every": 10, "nonlinearity": 0.5,
-                 "blowup_threshold": 1e3, "drift_tol": 1e-3}
+                 "blowup_threshold": 1e3, "drift_tol": 1e-3, "tune_cache": None}
     bad = kg.kg_options(7, 0, 1.0, 0.0, 0.0)
     assert kg.lib.kg_set_options(C.byref(bad)) == kg.KG_EINVAL
     bad = kg.kg_options(0, -1, 1.0, 0.0, 0.0)
@@ -63,6 +63,22 @@ def test_options_round_trip_and_validation(kg):
     assert kg.lib.kg_set_options(C.byref(bad)) == kg.KG_EINVAL
     kg.kg_set_options()
     assert kg.kg_get_options()["precision"] == kg.KG_DF64
+
+
+def test_tune_cache_path_through_options(kg, tmp_path):
+    """the ensemble autotuner's cache file can be named through kg_set_options: the library
+    keeps its own copy, NULL leaves it as set, "" clears it, and kg_ens_set_tune_cache is the
+    same setting"""
+    path = str(tmp_path / "tune.txt")
+    kg.kg_set_options(tune_cache=path)
+    assert kg.kg_get_options()["tune_cache"] == path
+    kg.kg_set_options(energy_every=5)                  # NULL: the file stays
+    assert kg.kg_get_options()["tune_cache"] == path
+    assert kg.lib.kg_ens_set_tune_cache(b"other.txt") == kg.KG_OK
+    assert kg.kg_get_options()["tune_cache"] == "other.txt"
+    kg.kg_set_options(tune_cache="")                   # "": no file
+    assert kg.kg_get_options()["tune_cache"] is None
+    kg.kg_set_options()
 
 
 def test_scheme_round_trip_and_validation(kg):
