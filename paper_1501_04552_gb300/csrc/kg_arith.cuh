@@ -402,7 +402,9 @@ struct PrecDF {
         return make_float4(s.x, __uint_as_float(__float_as_uint(s.y) ^ m), s.z, __uint_as_float(__float_as_uint(s.w) ^ m));
     }
     // the elementwise operations on both components at once, lane by lane as the scalar
-    // forms (df_scale2, cube, df_add_lazy); sign flips are products with +-1, exact
+    // forms (df_scale2, cube, df_add_lazy); sign flips are products with +-1, exact.  The x
+    // pass keeps its 1/N^3 scale and its cube scalar: with these packed forms there ptxas
+    // spilled 432 bytes per thread at 64 registers (24 with the scalar ones)
     static __device__ __forceinline__ cx<R> cscale2(cx<R> a, double p2) {
         const float2 f = make_float2((float)p2, (float)p2);
         dfc x = split(a);
