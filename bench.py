@@ -48,9 +48,9 @@ PAPER_TABLE1 = [("Hornet", 12288, 0.319), ("Juqueen", 262144, 0.350), ("Stampede
 # DRAM bytes (read + write) per launch of a step kernel at 512^3, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; the capture is summarised under
 # profiles/), valid only for the kernel sources it was taken on: KERNEL_SOURCES hashed
-TRAFFIC_512 = {("df64", "x"): 2099869952, ("df64", "yf"): 2096266752, ("df64", "z"): 5455485952,
-               ("df64", "yi"): 2096291072}
-TRAFFIC_SOURCES_SHA = "bf518d687a4e2659"
+TRAFFIC_512 = {("df64", "x"): 2099839488, ("df64", "yf"): 2096962304, ("df64", "z"): 5455137792,
+               ("df64", "yi"): 2096292352}
+TRAFFIC_SOURCES_SHA = "00869fe2215bc89a"
 KERNEL_SOURCES = ["kg_arith.cuh", "kg_fft.cuh", "kg_kernels.cuh", "kg_complex.cuh", "kg_launch_impl.cuh"]
 
 
@@ -338,15 +338,22 @@ def main():
 
     def timed_steps(prec, steps, warmup):
         """warm-up, then `steps` timed steps with the energy evaluated whenever the level
-        reaches a multiple of ENERGY_EVERY (the workload's cadence, counted from level 0).
-        The warm-up runs the same kernels, an energy evaluation included, so that no kernel
-        is loaded for the first time inside the timed region."""
+        reaches a multiple of ENERGY_EVERY (the workload's cadence, counted from level 0)
+        inside the timed region: an evaluation runs the next step's x pass ahead of time, so
+        one at the last level would time work of a step beyond the region.  The warm-up runs
+        the same kernels, an energy evaluation included, so that no kernel is loaded for the
+        first time inside the timed region."""
         kg.kg_set_options(precision=prec, energy_every=ENERGY_EVERY)
         d_u0 = torch.from_numpy(u0).to(f"cuda:{local}")
         kg.kg_init_device(NG, L_BOX, DT, d_u0, None)
         del d_u0
-        kg.kg_step(warmup)
-        kg.kg_energy(allow_drift=True)
+        # the warm-up's energy evaluation comes one step before its end: kg_energy runs the next
+        # step's x pass ahead (kg_step then skips it), and that step still belongs to the warm-up,
+        # so the timed region holds the whole work of its steps
+        if warmup >= 1:
+            kg.kg_step(warmup - 1)
+            kg.kg_energy(allow_drift=True)
+            kg.kg_step(1)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
@@ -359,7 +366,7 @@ def main():
             kg.kg_step(k)
             level += k
             left -= k
-            if level % ENERGY_EVERY == 0:
+            if level % ENERGY_EVERY == 0 and left > 0:
                 energies.append(kg.kg_energy(allow_drift=True))
         e1.record(stream)
         e1.synchronize()
@@ -379,6 +386,7 @@ def main():
     value = replicas.throughput(args.steps, world, ms * 1e-3)
 
     # per-kernel device times (CUDA events on the library's stream) for the roofline
+    kg.kg_step(1)   # a step whose x pass an energy evaluation ran ahead is not timed below
     names, k_avg = kernel_groups([t / args.steps for t in kg.kg_step_timed(args.steps)])
     k_bytes, step_bytes = algorithmic_bytes(prec, NG)
     dom = int(np.argmax(k_avg))
@@ -448,6 +456,7 @@ def main():
                 continue
             steps = ENERGY_EVERY * max(1, args.steps // (8 if other == "fp64" else 1) // ENERGY_EVERY)
             o_ms = timed_steps(other, steps, ENERGY_EVERY)
+            kg.kg_step(1)
             o_names, o_k = kernel_groups([t / steps for t in kg.kg_step_timed(steps)])
             o_bytes, o_step_bytes = algorithmic_bytes(other, NG)
             extras[other] = {"steps_per_s": round(steps / (o_ms * 1e-3), 2), "ms_per_step": round(o_ms / steps, 4),
@@ -551,8 +560,9 @@ def xy_fused_point(kg, stream, torch, u0, NG, local, peak):
         d_u0 = torch.from_numpy(u0).to(f"cuda:{local}")
         kg.kg_init_device(NG, L_BOX, DT, d_u0, None)
         del d_u0
-        kg.kg_step(5)
+        kg.kg_step(4)
         kg.kg_energy(allow_drift=True)
+        kg.kg_step(1)   # takes the x pass the energy evaluation ran ahead
         stream.synchronize()
         steps = 2 * ENERGY_EVERY
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

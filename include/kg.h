@@ -86,7 +86,13 @@ int kg_init_device(int N, double L, double dt, const double* d_u0, const double*
 int kg_step(int n);
 
 /* Synchronise and write E^{n-1/2} at the current level n (definition above).
- * Returns KG_EDRIFT (with *E written) when the drift watchdog trips. */
+ * Returns KG_EDRIFT (with *E written) when the drift watchdog trips.  P^n needs u^n, which
+ * only the next step's x pass forms: for a real field stepped by separate passes this call
+ * runs that x pass now (its blow-up check of u^n included, so a blow-up at level n shows in
+ * kg_status from here on) and the next kg_step / kg_step_timed skips it, so an energy
+ * evaluation costs no extra pass; otherwise (complex field, fused xy form, frozen state) a
+ * read-only pass or the FP64 state supplies P^n.  A second call at the same level returns
+ * the same value. */
 int kg_energy(double* E);
 
 /* Synchronise and write u^n (N^3 doubles, [z][y][x]) into caller-owned host memory. */

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -81,6 +82,9 @@ struct Ctx {
     cudaGraphExec_t xy_graph = nullptr;     // one captured step of the fused xy form (inverse y included)
     long long launched = 0;                 // steps enqueued so far
     bool plain_done = false;                // a step of the separate-pass form ran outside a graph
+    bool x_ahead = false;                   // kg_energy ran the next step's x pass (kg_step skips it)
+    long long e_level = -1;                 // level of the last kg_energy result, and the result
+    double e_value = 0.0;
 };
 
 Ctx* g_ctx = nullptr;
@@ -230,6 +234,8 @@ int reuse_ctx(Ctx* c, double L, double dt, Ctx** out) {
     c->xy_graph = nullptr;
     c->launched = 0;
     c->plain_done = false;
+    c->x_ahead = false;
+    c->e_level = -1;
     const int N = c->N;
     const int m2max = 3 * (N / 2) * (N / 2);
     if (c->tw != (void*)c->tw64) release(c, c->tw, c->pl->store_bytes * N);
@@ -431,7 +437,8 @@ int init_common_c(int N, double L, double dt, const double* u0, const double* v0
 // every step of a kg_step call but its first); it ends with the z pass and leaves W
 // y-forward, so the caller ends the call with one inverse y pass (xy_close).  Its time
 // goes to the x slot; the forward and inverse y slots stay empty.
-int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms, int xy = 0) {
+// skip_x: the x pass (and its finaliser) already ran for this step (kg_energy ran it ahead).
+int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms, int xy = 0, bool skip_x = false) {
     const int N = c->N, NH = c->NH;
     const double h = c->L / N;
     const double p_norm = c->lam * h * h * h / 4.0;
@@ -441,7 +448,13 @@ int launch_step(Ctx* c, cudaStream_t st, bool timed, float* ms, int xy = 0) {
     const size_t yps = (size_t)N * NX, zrs = (size_t)N * NX;
     auto col = c->cplx ? c->pl->colc : c->pl->col;
     if (timed) KG_CK(cudaEventRecord(c->ev[0], st));
-    if (xy) {
+    if (skip_x) {
+        // W already holds the x pass's output for this step; its max |u| becomes the step's
+        // (k_fin_x kept it in maxabs_peek; a frozen state keeps its value, as k_fin_x would)
+        char* d = reinterpret_cast<char*>(c->dev);
+        KG_CK(cudaMemcpyAsync(d + offsetof(KgDev, maxabs_last), d + offsetof(KgDev, maxabs_peek), sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+    } else if (xy) {
         // (inverse y,) x pass, forward y of every z-plane in one cluster launch
         KG_CK(c->pl->xy_fused(N, xy == 2, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
         KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->xy_parts(N), c->dev, p_norm, st));
@@ -634,7 +647,15 @@ int kg_step(int n) {
     if (!c) return fail(KG_ESTATE, "kg_step before kg_init");
     if (n < 0) return fail(KG_EINVAL, "n < 0");
     cudaStream_t st = stream_of(c);
-    const long long passes = (long long)n * passes_per_step(c);
+    long long passes = (long long)n * passes_per_step(c);
+    if (c->x_ahead && passes > 0) {
+        // the first step's x pass ran in kg_energy: the rest of that step, outside the graphs
+        c->x_ahead = false;
+        const int rc = launch_step(c, st, false, nullptr, 0, true);
+        if (rc) return rc;
+        c->launched++;
+        passes--;
+    }
     if (use_xy(c) && passes > 0) {
         // first step without the inverse y transforms (W holds the y-inverse between
         // calls), the others from the captured fused step, then one inverse y pass
@@ -672,7 +693,14 @@ int kg_step_timed(int n, float* ms) {
     if (n < 0 || !ms) return fail(KG_EINVAL, "bad arguments");
     for (int p = 0; p < 6; p++) ms[p] = 0.f;
     cudaStream_t st = stream_of(c);
-    const long long passes = (long long)n * passes_per_step(c);
+    long long passes = (long long)n * passes_per_step(c);
+    if (c->x_ahead && passes > 0) {
+        c->x_ahead = false;
+        const int rc = launch_step(c, st, true, ms, 0, true);
+        if (rc) return rc;
+        c->launched++;
+        passes--;
+    }
     const bool xy = use_xy(c);
     for (long long i = 0; i < passes; i++) {
         int rc = launch_step(c, st, true, ms, xy ? (i == 0 ? 1 : 2) : 0);
@@ -696,6 +724,14 @@ int kg_energy(double* E) {
     if (rc) return rc;
     const long long n = d.level;
     double Q, Pm, Pn;
+    if (c->e_level == n) {
+        // asked again at the same level (after an x pass run ahead W no longer holds u^n's
+        // transform to peek at): the value computed then
+        *E = c->e_value;
+        if (g_opt.drift_tol > 0.0 && c->have_E0 && std::fabs(*E - c->E0) > g_opt.drift_tol * std::fabs(c->E0))
+            return fail(KG_EDRIFT, "energy drift beyond drift_tol");
+        return KG_OK;
+    }
     // Q^{n-1/2}
     if (d.Q_last_level == n - 1) {
         Q = d.Q_last;
@@ -715,8 +751,22 @@ int kg_energy(double* E) {
         rc = p_from_state(c, true, &Pm);
         if (rc) return rc;
     }
-    // P^n: from W (which holds the yz-inverse of uh^n) unless the state froze
-    if (!d.frozen) {
+    // P^n: from W (which holds the yz-inverse of uh^n) unless the state froze.  For a real
+    // field stepped by separate passes, the next step's x pass runs now with P^n recorded
+    // (it forms u^n anyway) and kg_step skips it; otherwise a read-only peek pass.
+    if (!d.frozen && !c->cplx && !use_xy(c) && !c->x_ahead) {
+        const int one = 1;
+        KG_CK(cudaMemcpyAsync(reinterpret_cast<char*>(c->dev) + offsetof(KgDev, record_p), &one, sizeof(int),
+                              cudaMemcpyHostToDevice, st));
+        KG_CK(c->pl->pass_x(N, MODE_STEP, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam, st));
+        KG_CK(launch_fin_x(c->part_sum, c->part_max, c->pl->x_parts(N), c->dev, c->lam * h * h * h / 4.0, st));
+        c->x_ahead = true;
+        KgDev d2;
+        rc = read_dev(c, &d2);
+        if (rc) return rc;
+        if (d2.P_last_level != n) return fail(KG_ECUDA, "kg_energy: the x pass run ahead recorded no P");
+        Pn = d2.P_last;
+    } else if (!d.frozen) {
         if (c->cplx) {
             KG_CK(c->pl->passc_x(N, MODE_PEEK, c->W, c->dev, c->part_sum, c->part_max, c->tw, inv_n3(N), c->lam,
                                  st));
@@ -737,6 +787,8 @@ int kg_energy(double* E) {
         if (rc) return rc;
     }
     *E = Q - 0.5 * (Pm + Pn);
+    c->e_level = n;
+    c->e_value = *E;
     if (!c->have_E0) {
         c->have_E0 = true;
         c->E0 = *E;

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kXThreads, XcMinBlocks<P>::value) k_pass_xc(ty
     const int li = threadIdx.x / T, j = threadIdx.x % T;
     const size_t line = (size_t)blockIdx.x * X::LPC + li;
     LineSmemX<P, X::CTA_SYNC> lsm{sm + li * X::PADN, 1u + (unsigned)li, (unsigned)T};
-    const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev);
+    const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev) || dev->record_p;
     const R rlam = P::from_f64(lam);
     S* __restrict__ L = W + line * N;
     Stats<P> st;

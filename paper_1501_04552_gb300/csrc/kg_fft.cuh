@@ -494,7 +494,7 @@ struct KgDev {
     int status;               // nonzero: a device-side check failed
     int scheme;               // KG_SCHEME_EQ2 (0) or KG_SCHEME_COMPOSED4 (1)
     int sub;                  // composed scheme: substep 0..2 of the current step
-    int pad1;
+    int record_p;             // 1: the next x pass records P^l whatever energy_every says (cleared by k_fin_x)
 };
 
 __device__ __forceinline__ bool kg_recording(const KgDev* dev) {

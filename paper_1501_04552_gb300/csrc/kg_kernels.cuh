@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kXThreads, XMinBlocks<P>::value) k_pass_x(type
     __shared__ double red[96];
 
     const int li = threadIdx.x / T, j = threadIdx.x % T;
-    const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev);
+    const bool want_sum = (MODE == MODE_PEEK) || kg_recording(dev) || dev->record_p;
     const typename P::R rlam = P::from_f64(lam);
     Stats<P> st;
     st.init();
@@ -815,13 +815,18 @@ __global__ void __launch_bounds__(kFinThreads) k_fin_x(const double* part_sum, c
                                                        KgDev* dev, double p_norm) {
     NSum acc;
     double mx;
-    fin_reduce(kg_recording(dev) ? part_sum : nullptr, part_max, count, acc, mx);
+    // record_p marks the next step's x pass run ahead by kg_energy: it records P^l, and its
+    // max |u| waits in maxabs_peek until that step runs (kg_status reports the last step's)
+    const bool ahead = dev->record_p != 0;   // read by every thread before fin_reduce's barriers
+    const bool rec = kg_recording(dev) || ahead;
+    fin_reduce(rec ? part_sum : nullptr, part_max, count, acc, mx);
     if (dev->complex_field) mx = sqrt(mx);   // the keys were |u|^2
     // the composed scheme checks the field at integer times only (its first substep)
     if (threadIdx.x == 0 && dev->sub == 0) {
         if (!dev->frozen) {
-            dev->maxabs_last = mx;
-            if (kg_recording(dev)) {
+            if (ahead) dev->maxabs_peek = mx;
+            else dev->maxabs_last = mx;
+            if (rec) {
                 dev->P_last = p_norm * acc.value();
                 dev->P_last_level = dev->level;
             }
@@ -831,6 +836,7 @@ __global__ void __launch_bounds__(kFinThreads) k_fin_x(const double* part_sum, c
             }
         }
     }
+    if (threadIdx.x == 0) dev->record_p = 0;
 }
 
 // after a peek x pass

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(XyShape<N, CL>::NT, XyShape<N, CL>::MINB)
     const int ncols = rank == CL - 1 ? CW + 1 : CW;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NWARPS = X::NT / 32;
-    const bool want_sum = kg_recording(dev);
+    const bool want_sum = kg_recording(dev) || dev->record_p;
     const float rlam = P::from_f64(lam);
     Stats<P> st;
     st.init();
