@@ -150,6 +150,20 @@ def df64_step_ops(n):
     return x + 4 * n * n * (n // 2 + 1) * f
 
 
+def step_schedule(start, steps, every):
+    """the kg_step chunks of a timed region that starts at level `start` and runs `steps`
+    steps, and after which of them the energy is evaluated: at every level that is a multiple
+    of `every`, except the last level of the region (an evaluation runs the next step's x pass
+    ahead of time, work of a step outside the region)"""
+    out, level, left = [], start, steps
+    while left > 0:
+        k = min(left, every - level % every)
+        level += k
+        left -= k
+        out.append((k, level % every == 0 and left > 0))
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -360,13 +374,9 @@ def main():
         torch.cuda.synchronize()
         e0.record(stream)
         energies = []
-        level, left = warmup, steps
-        while left > 0:
-            k = min(left, ENERGY_EVERY - level % ENERGY_EVERY)
+        for k, evaluate in step_schedule(warmup, steps, ENERGY_EVERY):
             kg.kg_step(k)
-            level += k
-            left -= k
-            if level % ENERGY_EVERY == 0 and left > 0:
+            if evaluate:
                 energies.append(kg.kg_energy(allow_drift=True))
         e1.record(stream)
         e1.synchronize()

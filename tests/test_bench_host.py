@@ -51,3 +51,19 @@ def test_traffic_guard(bench, monkeypatch):
     assert bench.measured_traffic("df64", "z", 512) is None
     monkeypatch.undo()
     assert bench.measured_traffic("df64", "z", 256) is None
+
+
+def test_step_schedule(bench):
+    # the headline: 5 warm-up steps, 20 timed, the energy every 10 levels
+    assert bench.step_schedule(5, 20, 10) == [(5, True), (10, True), (5, False)]
+    # a region that ends on a multiple of the cadence does not evaluate there
+    assert bench.step_schedule(10, 20, 10) == [(10, True), (10, False)]
+    assert bench.step_schedule(10, 10, 10) == [(10, False)]
+    for start in range(0, 25):
+        for steps in range(1, 45):
+            sched = bench.step_schedule(start, steps, 10)
+            assert sum(k for k, _ in sched) == steps and all(k >= 1 for k, _ in sched)
+            level = start
+            for k, ev in sched:
+                level += k
+                assert ev == (level % 10 == 0 and level < start + steps)
